@@ -1,0 +1,182 @@
+/*
+ * libcholdiff -- blocked Cholesky factorisation and its forward- and
+ * reverse-mode derivatives on one GB300 GPU (sm_103a).
+ *
+ * The operations follow I. Murray, "Differentiation of the Cholesky
+ * decomposition" (arXiv:1602.07527):
+ *   cd_chol_fwd       Sec. 4.2 chol_blocked      (LAPACK DPOTRF):  Sigma -> L
+ *   cd_chol_fwd_sens  Sec. 4.2 chol_blocked_fwd  (forward mode):   (L, Sigma_dot) -> L_dot
+ *   cd_chol_rev       Sec. 4.2 chol_blocked_rev  (reverse mode):   (L, L_bar) -> tril(Sigma_bar)
+ * with the problem statement of Sec. 2 (forward mode L_dot(L, Sigma_dot),
+ * reverse mode Sigma_bar(L, L_bar)) and the symbolic results of Sec. 3
+ * (Eqs. symfwd, symrev, symrevtril) as their exact meaning.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every entry point
+ * ---------------------------------------------------------------------------
+ * Layout.  Every matrix is dense FP64, ROW-MAJOR, element (i, j) at
+ *   M[i * ld + j], 0 <= i, j < n, with leading dimension ld >= n (in
+ *   elements).  Pointers are DEVICE pointers on the handle's device and must
+ *   be 8-byte aligned.  Only the lower triangle (i >= j) of an input is read.
+ *   Only the lower triangle of an output is written, except that
+ *   cd_chol_rev with CD_OUT_SYM also writes the strict upper triangle.
+ *   The strictly upper triangle is otherwise neither read nor written.
+ *
+ * In place.  As in the paper (Sec. 4.1-4.2), each routine overwrites its
+ *   input array: cd_chol_fwd turns tril(Sigma) into L, cd_chol_fwd_sens turns
+ *   tril(Sigma_dot) into L_dot, cd_chol_rev turns L_bar into tril(Sigma_bar).
+ *   L must not overlap the in/out array.
+ *
+ * Meaning of Sigma_bar.  tril(Sigma_bar) holds, for i > j, the derivative of
+ *   f with respect to the tied pair Sigma_ij = Sigma_ji, and on the diagonal
+ *   d f / d Sigma_ii (Eq. symrevtril).  CD_OUT_SYM instead returns the full
+ *   symmetric matrix of Eq. symrev, S + S^T - diag(S), whose strict upper
+ *   triangle mirrors the strict lower one.  The gradient in the convention of
+ *   torch.linalg.cholesky's backward is (tril + tril^T)/2 of the CD_OUT_TRIL
+ *   result.
+ *
+ * Blocking.  options->nb (the paper's N_b, >= 1) is the block size; 0 picks
+ *   a default.  The forward routines put a short block last and the reverse
+ *   routine puts it first (top-left), as the paper does (Sec. 4.2).  Blocking
+ *   only reorders rounding: every nb gives the same exact result.
+ *
+ * Precision.  CD_FP64 does all arithmetic in FP64.  CD_MIXED_* keeps the
+ *   diagonal-tile work (factorisation, level-2 derivative loops, diagonal
+ *   block inverses, the Phi / halving steps) in FP64 and runs the large
+ *   off-diagonal products on BF16 tensor cores with operands split into two
+ *   (x = hi + lo, 3 products) or three (6 products) BF16 terms and FP32
+ *   accumulation; inputs and outputs stay FP64 in memory.
+ *
+ * Asynchrony and errors.  Every compute call is enqueued on `stream` (a
+ *   cudaStream_t, NULL for the legacy default stream) and returns without
+ *   waiting.  The return value reports argument errors (CD_EINVAL), workspace
+ *   allocation failure (CD_ENOMEM) and launch failures (CD_ECUDA) detected on
+ *   the host.  Errors found on the device (a bounded wait that ran out, an
+ *   inconsistent tile) set the handle's device error word, readable with
+ *   cd_get_last_device_error after the stream has been synchronised.
+ *   n == 0 is a valid no-op.
+ *
+ * Ownership.  The caller owns every matrix, info array and stream.  The
+ *   handle owns its workspace (grown on demand with cudaMalloc, released by
+ *   cd_destroy) and must not be used by two host threads at once; calls that
+ *   share a handle must be ordered on one stream (they share its workspace).
+ */
+#ifndef LIBCHOLDIFF_H
+#define LIBCHOLDIFF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  Positive values are never returned by the host calls; the
+ * factorisation's pivot report goes to the device `info` word instead. */
+#define CD_OK 0
+#define CD_EINVAL (-1)   /* bad argument: n < 0, ld < n, nb < 0, NULL pointer ... */
+#define CD_ENOMEM (-2)   /* workspace allocation failed                           */
+#define CD_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed          */
+#define CD_ETIMEOUT (-4) /* device word: a bounded device-side wait ran out       */
+
+typedef enum {
+  CD_FP64 = 0,          /* all FP64 (DFMA)                                    */
+  CD_MIXED_BF16X3 = 1,  /* products as hi*hi + hi*lo + lo*hi, BF16 in, FP32 acc */
+  CD_MIXED_BF16X6 = 2   /* three-term split, 6 BF16 products, FP32 accumulate  */
+} cd_precision;
+
+typedef enum {
+  CD_OUT_TRIL = 0, /* tril(Sigma_bar), Eq. symrevtril; strict upper untouched */
+  CD_OUT_SYM = 1   /* full symmetric Sigma_bar of Eq. symrev                   */
+} cd_output;
+
+typedef struct {
+  int nb;               /* block size N_b; 0 = library default                 */
+  int prec;             /* a cd_precision value                                */
+  int out;              /* a cd_output value (cd_chol_rev only)                */
+  long long spin_limit; /* bound on device-side wait iterations; 0 = default   */
+} cd_options;
+
+typedef struct cd_handle cd_handle;
+
+/* Create a handle bound to CUDA device `device`.  *h receives the handle.
+ * Returns CD_OK, CD_EINVAL (h NULL or bad device) or CD_ECUDA. */
+int cd_create(cd_handle **h, int device);
+
+/* Release the handle and its workspace.  The caller must first make sure no
+ * work enqueued with the handle is still running.  NULL is accepted. */
+int cd_destroy(cd_handle *h);
+
+/* Fill *opt with the defaults (nb 0, CD_FP64, CD_OUT_TRIL, default spin limit). */
+void cd_options_default(cd_options *opt);
+
+/* Bytes of workspace a call of size n_max with these options may use; a
+ * caller may pre-grow the handle with cd_reserve to keep later calls from
+ * allocating. */
+int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes);
+
+/* Grow the handle's workspace to at least `bytes` now (synchronous cudaMalloc). */
+int cd_reserve(cd_handle *h, size_t bytes);
+
+/*
+ * Blocked Cholesky factorisation (Sec. 4.2 chol_blocked, mirroring DPOTRF):
+ * overwrites tril(A) (holding tril(Sigma), n x n, leading dimension lda)
+ * with L, Sigma = L L^T.  info (device int*, may be NULL) receives 0 on
+ * success or the 1-based index j of the first column whose pivot
+ * Sigma_jj - sum_k L_jk^2 is not positive or not a number (LAPACK's info);
+ * L is then unspecified from that column on.  No pivoting.
+ */
+int cd_chol_fwd(cd_handle *h, int n, double *A, long long lda,
+                const cd_options *opt, void *stream, int *info);
+
+/*
+ * Reverse mode (Sec. 4.2 chol_blocked_rev; exact meaning Eq. symrevtril):
+ * given the factor L (lower, n x n, ldl) and tril(Abar) = L_bar (n x n,
+ * lda), overwrites tril(Abar) with tril(Sigma_bar) (or the full symmetric
+ * Sigma_bar of Eq. symrev with CD_OUT_SYM).  L's diagonal must be nonzero.
+ */
+int cd_chol_rev(cd_handle *h, int n, const double *L, long long ldl,
+                double *Abar, long long lda, const cd_options *opt, void *stream);
+
+/*
+ * Forward mode (Sec. 4.2 chol_blocked_fwd; exact meaning Eq. symfwd):
+ * given L and tril(Adot) = tril(Sigma_dot) of the symmetric perturbation
+ * Sigma_dot, overwrites tril(Adot) with L_dot = L Phi(L^{-1} Sigma_dot L^{-T}).
+ */
+int cd_chol_fwd_sens(cd_handle *h, int n, const double *L, long long ldl,
+                     double *Adot, long long lda, const cd_options *opt, void *stream);
+
+/*
+ * Batched variants over `batch` independent problems of ragged sizes.
+ * n, A/L/Abar/Adot pointers and leading dimensions are HOST arrays of length
+ * `batch` (the pointers inside are device pointers); problem b has size
+ * n[b] >= 0 and leading dimension ld[b] >= n[b].  Problems are independent
+ * (Sec. 2: each is its own x -> Sigma -> L -> f chain); their work is
+ * interleaved on the device so small problems share the GPU.  info (device
+ * int array of length batch, may be NULL) receives each factorisation's info.
+ * Results equal those of the single-problem calls with the same options.
+ */
+int cd_chol_fwd_batched(cd_handle *h, int batch, const int *n, double *const *A,
+                        const long long *lda, const cd_options *opt, void *stream, int *info);
+int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *const *L,
+                        const long long *ldl, double *const *Abar, const long long *lda,
+                        const cd_options *opt, void *stream);
+int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L,
+                             const long long *ldl, double *const *Adot, const long long *lda,
+                             const cd_options *opt, void *stream);
+
+/* Read and clear the handle's device error word (synchronises the handle's
+ * device).  *code receives CD_OK or a negative CD_* code. */
+int cd_get_last_device_error(cd_handle *h, int *code);
+
+/* Number of kernel launches this handle has issued since creation (a
+ * counter kept on the host; used to report launch counts). */
+long long cd_launch_count(const cd_handle *h);
+
+/* Library version string. */
+const char *cd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBCHOLDIFF_H */
