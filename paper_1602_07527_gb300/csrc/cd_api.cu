@@ -1,0 +1,700 @@
+// libcholdiff host side: the C ABI of include/libcholdiff.h, the workspace
+// arena, and the block-column schedulers that issue the blocked algorithms
+// of Sec. 4.2 as grouped kernel launches on the caller's stream.
+//
+// Every operation is written once for a ragged batch of independent
+// problems; a single call is a batch of one.  At each block step the work of
+// all still-active problems goes into one grouped launch per kernel kind, so
+// small problems share the GPU.
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cd_internal.h"
+#include "cd_mixed.h"
+
+using namespace cd;
+
+namespace {
+
+constexpr int kDefaultNbSmall = 64;
+constexpr int kDefaultNbLarge = 128;
+constexpr size_t kPartBytes = size_t(64) << 20;  // split-K partial sums
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, off = 0;
+  void *take(size_t bytes) {
+    size_t o = align_up(off);
+    if (o + bytes > cap) return nullptr;
+    off = o + bytes;
+    return base + o;
+  }
+};
+
+int pick_nb(int n, const cd_options *opt) {
+  if (opt && opt->nb > 0) return opt->nb;
+  return n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall;
+}
+
+int nblocks(int n, int nb) { return (n + nb - 1) / nb; }
+
+// Workspace one problem of size n needs at one recursion level.
+size_t prob_bytes(int n, int nb) {
+  if (n <= 0) return 0;
+  return align_up(sizeof(double) * (size_t)nblocks(n, nb) * nb * nb) + align_up(sizeof(double) * (size_t)n * nb);
+}
+
+// Extra workspace of the recursive diagonal step (nb > kTileMax).
+size_t recursion_bytes(int nb) {
+  if (nb <= kTileMax) return 0;
+  return prob_bytes(nb, kTileMax) + align_up(sizeof(double) * (size_t)nb * nb) + 4 * kAlign;
+}
+
+struct Prob {
+  int n;
+  const double *L;  // factor (rev, sens); null for fwd
+  long long ldl;
+  double *X;  // in/out
+  long long ldx;
+  int *info;
+  double *dinv;  // nblocks * nb * nb (ld nb)
+  double *W;     // n * nb (ld nb)
+  int col0;      // global column of this (sub)problem's first column (info)
+};
+
+struct Ctx {
+  cd_handle *h;
+  cudaStream_t s;
+  const cd_options *opt;
+  double *part;
+  size_t part_cap;  // doubles
+  int target_ctas;
+  int err = CD_OK;
+  void check(cudaError_t e) {  // after a kernel launch
+    ++h->launches;
+    cuda(e);
+  }
+  void cuda(cudaError_t e) {  // after any other CUDA call
+    if (e != cudaSuccess && err == CD_OK) err = CD_ECUDA;
+  }
+};
+
+// Accumulates GEMMs of one kind into a grouped launch.
+struct GemmBatch {
+  Ctx &c;
+  GemmGroup g;
+  size_t part_used = 0;
+  GemmBatch(Ctx &ctx, int amode, int bmode, bool lower) : c(ctx) {
+    memset(&g, 0, sizeof(g));
+    g.amode = amode;
+    g.bmode = bmode;
+    g.lower = lower ? 1 : 0;
+  }
+  void add(int M, int N, int K, const double *A, long long lda, const double *B, long long ldb, const double *Cin,
+           long long ldcin, double *Cout, long long ldcout, double alpha, double beta) {
+    if (M <= 0 || N <= 0) return;
+    if (K <= 0 && beta == 1.0 && Cin == Cout && ldcin == ldcout) return;  // identity update
+    const int tm = (M + 63) / 64, tn = (N + 63) / 64;
+    const int tiles_eff = g.lower ? std::max(1, tm * (tm + 1) / 2) : tm * tn;
+    int splits = 1;
+    if (K > 0 && tiles_eff < c.target_ctas) {
+      splits = (c.target_ctas + tiles_eff - 1) / tiles_eff;
+      splits = std::min(splits, std::max(1, K / 256));
+      splits = std::min(splits, 64);
+    }
+    const size_t mn = (size_t)M * N;
+    if (splits > 1 && mn * splits > c.part_cap) splits = (int)std::max<size_t>(1, c.part_cap / mn);
+    if (splits > 1 && part_used + mn * splits > c.part_cap) flush();
+    int kchunk = std::max(K, 1);
+    if (splits > 1) {
+      kchunk = (K + splits - 1) / splits;
+      kchunk = (kchunk + 15) / 16 * 16;
+      splits = (K + kchunk - 1) / kchunk;
+    }
+    if (g.count == kMaxGemm) flush();
+    GemmDesc &d = g.d[g.count++];
+    d.A = A; d.B = B; d.Cin = Cin; d.Cout = Cout;
+    d.lda = lda; d.ldb = ldb; d.ldcin = ldcin; d.ldcout = ldcout;
+    d.alpha = alpha; d.beta = beta;
+    d.M = M; d.N = N; d.K = K; d.splits = splits; d.kchunk = kchunk;
+    d.tiles_m = tm; d.tiles_n = tn;
+    d.tile_begin = g.total_tiles;
+    d.part = nullptr;
+    if (splits > 1) {
+      d.part = c.part + part_used;
+      part_used += mn * splits;
+    }
+    g.total_tiles += tm * tn * splits;
+  }
+  void flush() {
+    if (g.count == 0) return;
+    c.check(launch_gemm_group(g, c.s));
+    bool red = false;
+    for (int p = 0; p < g.count; ++p) red |= g.d[p].splits > 1;
+    if (red) c.check(launch_reduce_group(g, c.s));
+    g.count = 0;
+    g.total_tiles = 0;
+    part_used = 0;
+  }
+  ~GemmBatch() { flush(); }
+};
+
+struct TileBatch {
+  Ctx &c;
+  TileOp op;
+  TileGroup g;
+  TileBatch(Ctx &ctx, TileOp o) : c(ctx), op(o) { memset(&g, 0, sizeof(g)); }
+  void add(const TileDesc &d) {
+    if (d.t <= 0) return;
+    if (g.count == kMaxTile) flush();
+    g.d[g.count++] = d;
+  }
+  void flush() {
+    if (g.count == 0) return;
+    c.check(launch_tile_group(op, g, c.s));
+    g.count = 0;
+  }
+  ~TileBatch() { flush(); }
+};
+
+TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double *inv, long long ldinv, int t,
+               int *info = nullptr, int col0 = 0) {
+  TileDesc d;
+  d.L = L; d.ldl = ldl; d.X = X; d.ldx = ldx; d.inv = inv; d.ldinv = ldinv;
+  d.t = t; d.info = info; d.col0 = col0;
+  return d;
+}
+
+// Forward declarations (recursive diagonal steps).
+void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
+void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
+void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
+
+// inv (t x t, ld ldinv, zero above the diagonal) = tril(D)^{-1}.
+// t <= kTileMax: one CTA; larger: split D = [D11 0; D21 D22] and use
+// inv21 = -inv22 (D21 inv11).
+void trtri_big(Ctx &c, const double *D, long long ldd, double *inv, long long ldinv, int t, Arena &ar) {
+  if (t <= kTileMax) {
+    TileBatch tb(c, T_TRTRI);
+    tb.add(tdesc(D, ldd, nullptr, 0, inv, ldinv, t));
+    return;
+  }
+  const int h1 = (t / 2 + 63) / 64 * 64, h2 = t - h1;
+  trtri_big(c, D, ldd, inv, ldinv, h1, ar);
+  trtri_big(c, D + (long long)h1 * ldd + h1, ldd, inv + (long long)h1 * ldinv + h1, ldinv, h2, ar);
+  size_t mark = ar.off;
+  double *T = (double *)ar.take(sizeof(double) * (size_t)h2 * h1);
+  if (!T) { c.err = CD_ENOMEM; return; }
+  {
+    GemmBatch gb(c, A_N, B_N, false);  // T = D21 inv11
+    gb.add(h2, h1, h1, D + (long long)h1 * ldd, ldd, inv, ldinv, nullptr, 0, T, h1, 1.0, 0.0);
+  }
+  {
+    GemmBatch gb(c, A_N, B_N, false);  // inv21 = -inv22 T  (inv22 lower, zero above)
+    gb.add(h2, h1, h2, inv + (long long)h1 * ldinv + h1, ldinv, T, h1, nullptr, 0, inv + (long long)h1 * ldinv,
+           ldinv, -1.0, 0.0);
+  }
+  // inv12 = 0
+  c.cuda(cudaMemset2DAsync(inv + h1, sizeof(double) * ldinv, 0, sizeof(double) * h2, h1, c.s));
+  ar.off = mark;
+}
+
+// Diagonal block inverse for every block of a partition of each problem.
+// rev_partition: blocks [max(0,k-nb), k) for k = n, n-nb, ... (short block
+// first); otherwise [j, min(n, j+nb)) (short block last).
+void precompute_dinv(Ctx &c, std::vector<Prob> &P, int nb, bool rev_partition, Arena &ar) {
+  TileBatch tb(c, T_TRTRI);
+  for (auto &p : P) {
+    const int nbk = nblocks(p.n, nb);
+    for (int s = 0; s < nbk; ++s) {
+      int j, k;
+      if (rev_partition) {
+        k = p.n - s * nb;
+        j = std::max(0, k - nb);
+      } else {
+        j = s * nb;
+        k = std::min(p.n, j + nb);
+      }
+      const int w = k - j;
+      double *inv = p.dinv + (size_t)s * nb * nb;
+      if (w <= kTileMax) {
+        tb.add(tdesc(p.L + (long long)j * p.ldl + j, p.ldl, nullptr, 0, inv, nb, w));
+      } else {
+        tb.flush();
+        trtri_big(c, p.L + (long long)j * p.ldl + j, p.ldl, inv, nb, w, ar);
+      }
+    }
+  }
+}
+
+bool bind_workspace(std::vector<Prob> &P, int nb, Arena &ar) {
+  for (auto &p : P) {
+    p.dinv = nullptr;
+    p.W = nullptr;
+    if (p.n <= 0) continue;
+    p.dinv = (double *)ar.take(sizeof(double) * (size_t)nblocks(p.n, nb) * nb * nb);
+    p.W = (double *)ar.take(sizeof(double) * (size_t)p.n * nb);
+    if (!p.dinv || !p.W) return false;
+  }
+  return true;
+}
+
+// ------------------------------- chol_blocked (Sec. 4.2) -------------------
+void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    {  // f1: D <- D - tril(R R^T)
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j;
+        double *R = p.X + (long long)j * p.ldx;
+        gb.add(w, w, j, R, p.ldx, R, p.ldx, R + j, p.ldx, R + j, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // f2: D <- chol_unblocked(D); inverse of D for f4
+      TileBatch tb(c, T_POTF2);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(nullptr, 0, D, p.ldx, p.dinv, nb, w, p.info, p.col0 + j));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_fwd(c, sub, kTileMax, ar);
+          trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    {  // f3: C <- C - B R^T
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j;
+        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.X + (long long)j * p.ldx, p.ldx, C, p.ldx, C, p.ldx,
+               -1.0, 1.0);
+      }
+    }
+    {  // f4: C <- C tril(D)^{-T}   (W = C Dinv^T, then copy back)
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv, nb, nullptr, 0, p.W, nb, 1.0, 0.0);
+      }
+    }
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+    }
+  }
+}
+
+// ------------------------------ chol_blocked_rev (Sec. 4.2) ----------------
+void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  precompute_dinv(c, P, nb, true, ar);
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  auto blk = [&](const Prob &p, int s, int &j, int &k) {
+    k = p.n - s * nb;
+    j = std::max(0, k - nb);
+    return k > 0;
+  };
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    {  // r1: C_bar <- C_bar D^{-1}   (into W)
+      GemmBatch gb(c, A_N, B_N, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv + (size_t)s * nb * nb, nb, nullptr, 0, p.W,
+               nb, 1.0, 0.0);
+      }
+    }
+    for (auto &p : P) {
+      int j, k;
+      if (!blk(p, s, j, k)) continue;
+      const int w = k - j, m = p.n - k;
+      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+    }
+    {  // r2: B_bar <- B_bar - C_bar R
+      GemmBatch gb(c, A_N, B_N, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Bb = p.X + (long long)k * p.ldx;
+        gb.add(m, j, w, p.W, nb, p.L + (long long)j * p.ldl, p.ldl, Bb, p.ldx, Bb, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // r3: D_bar <- tril(D_bar) - tril(C_bar^T C)
+      GemmBatch gb(c, A_T, B_N, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Db = p.X + (long long)j * p.ldx + j;
+        gb.add(w, w, m, p.W, nb, p.L + (long long)k * p.ldl + j, p.ldl, Db, p.ldx, Db, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)
+      TileBatch tb(c, T_REV);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        const double *D = p.L + (long long)j * p.ldl + j;
+        double *Db = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(D, p.ldl, Db, p.ldx, nullptr, 0, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, D, p.ldl, Db, p.ldx, nullptr, nullptr, nullptr, 0};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_rev(c, sub, kTileMax, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    {  // r5: R_bar <- R_bar - C_bar^T B - (D_bar + D_bar^T) R  ==  R_bar - G L[j:n, 0:j]
+      GemmBatch gb(c, A_SYM2, B_N, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *Rb = p.X + (long long)j * p.ldx;
+        gb.add(w, j, p.n - j, p.X + (long long)j * p.ldx + j, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Rb, p.ldx,
+               Rb, p.ldx, -1.0, 1.0);
+      }
+    }
+  }
+}
+
+// ------------------------------ chol_blocked_fwd (Sec. 4.2) ----------------
+void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  precompute_dinv(c, P, nb, false, ar);
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        const double *Rd = p.X + (long long)j * p.ldx;
+        const double *R = p.L + (long long)j * p.ldl;
+        double *Dd = p.X + (long long)j * p.ldx + j;
+        if (term == 0)
+          gb.add(w, w, j, Rd, p.ldx, R, p.ldl, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
+        else
+          gb.add(w, w, j, R, p.ldl, Rd, p.ldx, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
+      TileBatch tb(c, T_SENS);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        const double *D = p.L + (long long)j * p.ldl + j;
+        double *Dd = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_sens(c, sub, kTileMax, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    for (int term = 0; term < 2; ++term) {  // g3: C_dot <- C_dot - B_dot R^T - B R_dot^T
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *Cd = p.X + (long long)k * p.ldx + j;
+        if (term == 0)
+          gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Cd, p.ldx, Cd,
+                 p.ldx, -1.0, 1.0);
+        else
+          gb.add(m, w, j, p.L + (long long)k * p.ldl, p.ldl, p.X + (long long)j * p.ldx, p.ldx, Cd, p.ldx, Cd,
+                 p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // g4a: C_dot <- C_dot - C D_dot^T
+      GemmBatch gb(c, A_N, B_TL, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *Cd = p.X + (long long)k * p.ldx + j;
+        gb.add(m, w, w, p.L + (long long)k * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx, Cd, p.ldx, Cd,
+               p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // g4b: C_dot <- C_dot D^{-T}   (into W, then copy back)
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv + (size_t)s * nb * nb, nb, nullptr, 0, p.W,
+               nb, 1.0, 0.0);
+      }
+    }
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+    }
+  }
+}
+
+enum Op { OP_FWD, OP_REV, OP_SENS };
+
+size_t need_bytes(const int *n, int batch, int nb) {
+  size_t b = kPartBytes + recursion_bytes(nb) + kAlign;
+  for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb) + 2 * kAlign;
+  return b;
+}
+
+int ensure_ws(cd_handle *h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return CD_OK;
+  if (h->ws) {
+    cudaDeviceSynchronize();  // earlier calls may still use the old buffer
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return CD_ENOMEM;
+  }
+  h->ws_bytes = bytes;
+  return CD_OK;
+}
+
+int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, const long long *ldl,
+        double *const *X, const long long *ldx, const cd_options *opt_in, void *stream, int *info) {
+  if (!h || batch < 0 || (batch > 0 && (!n || !X || !ldx))) return CD_EINVAL;
+  cd_options opt;
+  cd_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.nb < 0 || opt.prec < CD_FP64 || opt.prec > CD_MIXED_BF16X6 || opt.out < CD_OUT_TRIL ||
+      opt.out > CD_OUT_SYM)
+    return CD_EINVAL;
+  int nmax = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] < 0 || ldx[b] < std::max(1, n[b])) return CD_EINVAL;
+    if (n[b] > 0 && !X[b]) return CD_EINVAL;
+    if (op != OP_FWD) {
+      if (!L || !ldl) return CD_EINVAL;
+      if (n[b] > 0 && (!L[b] || ldl[b] < n[b])) return CD_EINVAL;
+    }
+    nmax = std::max(nmax, n[b]);
+  }
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op == OP_FWD && info && batch > 0) {
+    if (cudaMemsetAsync(info, 0, sizeof(int) * batch, s) != cudaSuccess) return CD_ECUDA;
+  }
+  if (nmax == 0) return CD_OK;
+  const int nb = pick_nb(nmax, &opt);
+  int rc = ensure_ws(h, need_bytes(n, batch, nb));
+  if (rc) return rc;
+
+  Arena ar;
+  ar.base = (char *)h->ws;
+  ar.cap = h->ws_bytes;
+  Ctx c{h, s, &opt, nullptr, 0, 2 * h->num_sms};
+  c.part = (double *)ar.take(kPartBytes);
+  c.part_cap = kPartBytes / sizeof(double);
+  std::vector<Prob> P;
+  P.reserve(batch);
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] == 0) continue;
+    Prob p{n[b], op == OP_FWD ? nullptr : L[b], op == OP_FWD ? 0 : ldl[b], X[b], ldx[b],
+           info ? info + b : nullptr, nullptr, nullptr, 0};
+    P.push_back(p);
+  }
+  if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
+  if (opt.prec != CD_FP64 && !mixed_available()) return CD_EINVAL;
+  switch (op) {
+    case OP_FWD: run_fwd(c, P, nb, ar); break;
+    case OP_REV: run_rev(c, P, nb, ar); break;
+    case OP_SENS: run_sens(c, P, nb, ar); break;
+  }
+  if (c.err) return c.err;
+  if (op == OP_REV && opt.out == CD_OUT_SYM)
+    for (auto &p : P) c.check(launch_mirror_lower(p.X, p.ldx, p.n, s));
+  return c.err;
+}
+
+bool g_init_done = false;
+
+}  // namespace
+
+extern "C" {
+
+const char *cd_version(void) { return "libcholdiff 0.1 (sm_103a)"; }
+
+void cd_options_default(cd_options *opt) {
+  if (!opt) return;
+  opt->nb = 0;
+  opt->prec = CD_FP64;
+  opt->out = CD_OUT_TRIL;
+  opt->spin_limit = 0;
+}
+
+int cd_create(cd_handle **h, int device) {
+  if (!h) return CD_EINVAL;
+  *h = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return CD_ECUDA;
+  }
+  if (device < 0 || device >= count) return CD_EINVAL;
+  DeviceGuard guard(device);
+  cd_handle *x = (cd_handle *)calloc(1, sizeof(cd_handle));
+  if (!x) return CD_ENOMEM;
+  x->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    free(x);
+    return CD_ECUDA;
+  }
+  x->num_sms = prop.multiProcessorCount;
+  x->smem_optin = prop.sharedMemPerBlockOptin;
+  if (tile_kernels_init() != cudaSuccess || mixed_init() != CD_OK) {
+    free(x);
+    return CD_ECUDA;
+  }
+  g_init_done = true;
+  if (cudaMalloc(&x->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(x->dev_err, 0, sizeof(int)) != cudaSuccess) {
+    free(x);
+    return CD_ECUDA;
+  }
+  *h = x;
+  return CD_OK;
+}
+
+int cd_destroy(cd_handle *h) {
+  if (!h) return CD_OK;
+  DeviceGuard guard(h->device);
+  if (h->ws) cudaFree(h->ws);
+  if (h->dev_err) cudaFree(h->dev_err);
+  free(h);
+  return CD_OK;
+}
+
+int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes) {
+  if (!h || !bytes || n_max < 0) return CD_EINVAL;
+  const int nb = pick_nb(n_max, opt);
+  *bytes = need_bytes(&n_max, 1, nb) + mixed_workspace_bytes(n_max, nb, opt ? opt->prec : CD_FP64);
+  return CD_OK;
+}
+
+int cd_reserve(cd_handle *h, size_t bytes) {
+  if (!h) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  return ensure_ws(h, bytes);
+}
+
+int cd_chol_fwd(cd_handle *h, int n, double *A, long long lda, const cd_options *opt, void *stream, int *info) {
+  double *X[1] = {A};
+  long long ld[1] = {lda};
+  return run(h, OP_FWD, 1, &n, nullptr, nullptr, X, ld, opt, stream, info);
+}
+
+int cd_chol_rev(cd_handle *h, int n, const double *L, long long ldl, double *Abar, long long lda,
+                const cd_options *opt, void *stream) {
+  const double *Lp[1] = {L};
+  long long ll[1] = {ldl};
+  double *X[1] = {Abar};
+  long long ld[1] = {lda};
+  return run(h, OP_REV, 1, &n, Lp, ll, X, ld, opt, stream, nullptr);
+}
+
+int cd_chol_fwd_sens(cd_handle *h, int n, const double *L, long long ldl, double *Adot, long long lda,
+                     const cd_options *opt, void *stream) {
+  const double *Lp[1] = {L};
+  long long ll[1] = {ldl};
+  double *X[1] = {Adot};
+  long long ld[1] = {lda};
+  return run(h, OP_SENS, 1, &n, Lp, ll, X, ld, opt, stream, nullptr);
+}
+
+int cd_chol_fwd_batched(cd_handle *h, int batch, const int *n, double *const *A, const long long *lda,
+                        const cd_options *opt, void *stream, int *info) {
+  return run(h, OP_FWD, batch, n, nullptr, nullptr, A, lda, opt, stream, info);
+}
+
+int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *const *L, const long long *ldl,
+                        double *const *Abar, const long long *lda, const cd_options *opt, void *stream) {
+  return run(h, OP_REV, batch, n, L, ldl, Abar, lda, opt, stream, nullptr);
+}
+
+int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L, const long long *ldl,
+                             double *const *Adot, const long long *lda, const cd_options *opt, void *stream) {
+  return run(h, OP_SENS, batch, n, L, ldl, Adot, lda, opt, stream, nullptr);
+}
+
+int cd_get_last_device_error(cd_handle *h, int *code) {
+  if (!h || !code) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  int v = 0;
+  if (cudaMemcpy(&v, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CD_ECUDA;
+  if (cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess) return CD_ECUDA;
+  *code = v;
+  return CD_OK;
+}
+
+long long cd_launch_count(const cd_handle *h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Internal declarations shared by the libcholdiff CUDA translation units.
+// Not installed; the public interface is include/libcholdiff.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/libcholdiff.h"
+
+namespace cd {
+
+// ---------------------------------------------------------------------------
+// Grouped FP64 GEMM: Cout = beta * Cin + alpha * op(A) op(B), for up to
+// kMaxGemm independent problems per launch (batched work shares one grid).
+// ---------------------------------------------------------------------------
+enum AMode { A_N = 0, A_T = 1, A_SYM2 = 2 };
+// A_N   : a(i,k) = A[i*lda + k]
+// A_T   : a(i,k) = A[k*lda + i]
+// A_SYM2: a(i,k) = symmetric view of a lower-stored matrix with doubled
+//         diagonal: A[i][k] (i > k), A[k][i] (i < k), 2 A[i][i] (i == k).
+//         This is G = X + X^T for X = tril(A), used by the reverse pass.
+enum BMode { B_N = 0, B_T = 1, B_TL = 2 };
+// B_N   : b(k,j) = B[k*ldb + j]
+// B_T   : b(k,j) = B[j*ldb + k]
+// B_TL  : b(k,j) = B[j*ldb + k] if j >= k else 0   (transpose of a lower matrix)
+
+struct GemmDesc {
+  const double *A, *B, *Cin;
+  double *Cout, *part;
+  long long lda, ldb, ldcin, ldcout;
+  double alpha, beta;
+  int M, N, K, splits;
+  int tiles_m, tiles_n, tile_begin, kchunk;
+};
+
+constexpr int kMaxGemm = 32;
+struct GemmGroup {
+  int count, total_tiles;
+  int amode, bmode, lower, pad_;
+  GemmDesc d[kMaxGemm];
+};
+
+// ---------------------------------------------------------------------------
+// One-CTA diagonal-tile kernels (t <= kTileMax, tile in shared memory).
+// ---------------------------------------------------------------------------
+constexpr int kTileMax = 128;
+
+struct TileDesc {
+  const double *L;  // factor tile (rev / sens / inverse), lower
+  double *X;        // in/out tile
+  double *inv;      // output: inverse of the factor tile, t x t full (ld = ldinv)
+  int *info;        // potf2: info word of the problem (may be null)
+  long long ldl, ldx, ldinv;
+  int t, col0;      // tile size; global column of the tile's first column
+};
+
+constexpr int kMaxTile = 48;
+struct TileGroup {
+  int count, pad_;
+  TileDesc d[kMaxTile];
+};
+
+enum TileOp { T_POTF2 = 0, T_REV = 1, T_SENS = 2, T_TRTRI = 3 };
+
+// ---------------------------------------------------------------------------
+// Mixed-precision (split-BF16 tcgen05) engine: see cd_mixed.cu.
+// ---------------------------------------------------------------------------
+struct MixedGemm;  // opaque
+
+}  // namespace cd
+
+struct cd_handle {
+  int device;
+  int num_sms;
+  size_t smem_optin;
+  void *ws;
+  size_t ws_bytes;
+  int *dev_err;
+  long long launches;
+};
+
+namespace cd {
+// Launchers (cd_f64_kernels.cu).  All return cudaError_t of the launch.
+cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s);
+cudaError_t launch_reduce_group(const GemmGroup &g, cudaStream_t s);
+cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s);
+cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, int rows,
+                        int cols, cudaStream_t s);
+cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
+cudaError_t tile_kernels_init();
+}  // namespace cd

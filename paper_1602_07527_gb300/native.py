@@ -1,0 +1,249 @@
+"""ctypes binding of libcholdiff (include/libcholdiff.h).
+
+Argument marshalling only: every matrix operation runs in the CUDA library.
+Tensors must be CUDA float64, 2-D, row-major with unit column stride (the
+row stride is passed as the leading dimension).  Calls are enqueued on the
+current torch CUDA stream of the tensor's device and return without waiting.
+There is no CPU fallback: if the library is missing the first call raises.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcholdiff.so")
+
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT = 0, -1, -2, -3, -4
+_ERR = {CD_EINVAL: "invalid argument", CD_ENOMEM: "workspace allocation failed",
+        CD_ECUDA: "CUDA error", CD_ETIMEOUT: "device-side wait timed out"}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+OUT = {"tril": 0, "sym": 1}
+
+
+class CholDiffError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_ERR.get(code, 'error')} (code {code})")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int),
+                ("spin_limit", ctypes.c_longlong)]
+
+
+_lib = None
+_lock = threading.Lock()
+_handles = {}
+
+_vp = ctypes.c_void_p
+_ll = ctypes.c_longlong
+_i = ctypes.c_int
+
+
+def lib():
+    """Load libcholdiff.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.cd_create.argtypes = [P(_vp), _i]
+        L.cd_destroy.argtypes = [_vp]
+        L.cd_options_default.argtypes = [P(Options)]
+        L.cd_options_default.restype = None
+        L.cd_workspace_size.argtypes = [_vp, _i, P(Options), P(ctypes.c_size_t)]
+        L.cd_reserve.argtypes = [_vp, ctypes.c_size_t]
+        L.cd_chol_fwd.argtypes = [_vp, _i, _vp, _ll, P(Options), _vp, _vp]
+        L.cd_chol_rev.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp]
+        L.cd_chol_fwd_sens.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp]
+        L.cd_chol_fwd_batched.argtypes = [_vp, _i, _vp, _vp, _vp, P(Options), _vp, _vp]
+        L.cd_chol_rev_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp]
+        L.cd_chol_fwd_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp]
+        L.cd_get_last_device_error.argtypes = [_vp, P(_i)]
+        L.cd_launch_count.argtypes = [_vp]
+        L.cd_launch_count.restype = _ll
+        L.cd_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of every entry point the header declares (for load checks)."""
+    return ["cd_create", "cd_destroy", "cd_options_default", "cd_workspace_size", "cd_reserve",
+            "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
+            "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
+            "cd_launch_count", "cd_version"]
+
+
+def handle(device=None):
+    """The library handle of a CUDA device (created on first use, kept for the process)."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    if dev is None:
+        dev = torch.cuda.current_device()
+    h = _handles.get(dev)
+    if h is None:
+        with _lock:
+            h = _handles.get(dev)
+            if h is None:
+                hp = _vp()
+                rc = lib().cd_create(ctypes.byref(hp), dev)
+                if rc != CD_OK:
+                    raise CholDiffError(rc, "cd_create")
+                h = hp.value
+                _handles[dev] = h
+    return h
+
+
+def options(nb=0, prec="fp64", out="tril", spin_limit=0):
+    o = Options()
+    lib().cd_options_default(ctypes.byref(o))
+    o.nb = int(nb)
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.out = OUT[out] if isinstance(out, str) else int(out)
+    o.spin_limit = int(spin_limit)
+    return o
+
+
+def _mat(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name} must be square 2-D, got {tuple(t.shape)}")
+    if t.shape[0] > 0 and (t.stride(1) != 1 or t.stride(0) < t.shape[0]):
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    return t.shape[0], max(1, t.stride(0))
+
+
+def _stream(dev):
+    return _vp(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _check(rc, what):
+    if rc != CD_OK:
+        raise CholDiffError(rc, what)
+
+
+def chol_fwd(A, nb=0, prec="fp64", info=None):
+    """In place: tril(A) = tril(Sigma) -> L (Sec. 4.2 chol_blocked).
+
+    Returns the device int32 tensor holding LAPACK-style info (0 = success,
+    j = first non-positive pivot, 1-based).
+    """
+    n, lda = _mat(A, "A")
+    dev = A.device
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+    o = options(nb, prec)
+    _check(lib().cd_chol_fwd(handle(dev), n, _vp(A.data_ptr()), lda, ctypes.byref(o), _stream(dev),
+                             _vp(info.data_ptr())), "cd_chol_fwd")
+    return info
+
+
+def chol_rev(L, Abar, nb=0, prec="fp64", out="tril"):
+    """In place: tril(Abar) = L_bar -> tril(Sigma_bar) (Sec. 4.2 chol_blocked_rev)."""
+    n, ldl = _mat(L, "L")
+    n2, lda = _mat(Abar, "Abar")
+    if n != n2 or L.device != Abar.device:
+        raise ValueError("L and Abar must have the same size and device")
+    o = options(nb, prec, out)
+    _check(lib().cd_chol_rev(handle(L.device), n, _vp(L.data_ptr()), ldl, _vp(Abar.data_ptr()), lda,
+                             ctypes.byref(o), _stream(L.device)), "cd_chol_rev")
+    return Abar
+
+
+def chol_fwd_sens(L, Adot, nb=0, prec="fp64"):
+    """In place: tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.2 chol_blocked_fwd)."""
+    n, ldl = _mat(L, "L")
+    n2, lda = _mat(Adot, "Adot")
+    if n != n2 or L.device != Adot.device:
+        raise ValueError("L and Adot must have the same size and device")
+    o = options(nb, prec)
+    _check(lib().cd_chol_fwd_sens(handle(L.device), n, _vp(L.data_ptr()), ldl, _vp(Adot.data_ptr()), lda,
+                                  ctypes.byref(o), _stream(L.device)), "cd_chol_fwd_sens")
+    return Adot
+
+
+def _arrays(mats, name):
+    ns, lds, ptrs = [], [], []
+    for t in mats:
+        n, ld = _mat(t, name)
+        ns.append(n)
+        lds.append(ld)
+        ptrs.append(t.data_ptr())
+    b = len(mats)
+    return (b, (_i * b)(*ns), (_ll * b)(*lds), (_vp * b)(*ptrs), ns)
+
+
+def chol_fwd_batched(As, nb=0, prec="fp64", info=None):
+    b, n, ld, p, _ = _arrays(As, "A")
+    if b == 0:
+        return info
+    dev = As[0].device
+    if info is None:
+        info = torch.zeros(b, dtype=torch.int32, device=dev)
+    o = options(nb, prec)
+    _check(lib().cd_chol_fwd_batched(handle(dev), b, n, p, ld, ctypes.byref(o), _stream(dev),
+                                     _vp(info.data_ptr())), "cd_chol_fwd_batched")
+    return info
+
+
+def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril"):
+    b, n, ldl, pl, ns = _arrays(Ls, "L")
+    b2, n2, lda, pa, ns2 = _arrays(Abars, "Abar")
+    if b != b2 or ns != ns2:
+        raise ValueError("L and Abar lists must match")
+    if b == 0:
+        return Abars
+    dev = Ls[0].device
+    o = options(nb, prec, out)
+    _check(lib().cd_chol_rev_batched(handle(dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
+           "cd_chol_rev_batched")
+    return Abars
+
+
+def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64"):
+    b, n, ldl, pl, ns = _arrays(Ls, "L")
+    b2, n2, lda, pa, ns2 = _arrays(Adots, "Adot")
+    if b != b2 or ns != ns2:
+        raise ValueError("L and Adot lists must match")
+    if b == 0:
+        return Adots
+    dev = Ls[0].device
+    o = options(nb, prec)
+    _check(lib().cd_chol_fwd_sens_batched(handle(dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
+           "cd_chol_fwd_sens_batched")
+    return Adots
+
+
+def launch_count(device=None):
+    return int(lib().cd_launch_count(handle(device)))
+
+
+def device_error(device=None):
+    code = _i()
+    _check(lib().cd_get_last_device_error(handle(device), ctypes.byref(code)), "cd_get_last_device_error")
+    return code.value
+
+
+def workspace_size(n, nb=0, prec="fp64", device=None):
+    o = options(nb, prec)
+    out = ctypes.c_size_t()
+    _check(lib().cd_workspace_size(handle(device), int(n), ctypes.byref(o), ctypes.byref(out)),
+           "cd_workspace_size")
+    return out.value
+
+
+def reserve(nbytes, device=None):
+    _check(lib().cd_reserve(handle(device), int(nbytes)), "cd_reserve")
+
+
+def version():
+    return lib().cd_version().decode()
