@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the blocked Cholesky derivative path on one GB300 (or N
+independent replicas under torchrun).
+
+One step = one pass of the whole hot path on one synthetic problem:
+chol_fwd(Sigma) -> L, chol_fwd_sens(L, Sigma_dot) -> L_dot and
+chol_rev(L, L_bar) -> tril(Sigma_bar), with the in-place inputs restored from
+pristine device copies at the start of the step.  The headline value is the
+reverse pass's throughput, nominal 2 N^3 / 3 flops over its device time
+(CUDA events on the launching stream), at N = 8192 on a squared-exponential
+covariance (ell 0.3 on [0,1]^3, jitter 1e-4).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W]       # our CUDA path
+  python bench.py --impl reference ...                        # the CPU oracle
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chol_rev TFLOP/s @N=8192 (FP64 vs mixed, err vs FP64); served fwd+rev p99 latency"
+UNIT = "TFLOP/s"
+# FP64 is a plain-ALU (DFMA) path on GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+SE_SEED = 2
+
+
+def flops_fwd(n):
+    return n ** 3 / 3.0
+
+
+def flops_rev(n):
+    return 2.0 * n ** 3 / 3.0
+
+
+def flops_sens(n):
+    return 2.0 * n ** 3 / 3.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--cpu-n", type=int, default=6144, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self, backend):
+        import torch
+        import torch.distributed as dist
+        self.ws, self.rank, self.local = dist_env()
+        self.dist = dist if self.ws > 1 else None
+        self.torch = torch
+        if self.dist:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x):
+        if not self.dist:
+            return x
+        t = self.torch.tensor([float(x)], device="cuda" if self.torch.cuda.is_available() else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rev_sample(n):
+    import oracle
+    from paper_1602_07527_gb300 import workloads as W
+    S, Lb = W.large_se_case(n, SE_SEED)
+    L, info = oracle.chol_unblocked(S)
+    if info:
+        raise RuntimeError(f"oracle factorisation failed at column {info}")
+    t = time.perf_counter()
+    oracle.chol_unblocked_rev(L, Lb)
+    dt = time.perf_counter() - t
+    return dt, oracle.num_threads()
+
+
+def cpu_baseline(n):
+    dt, cores = oracle_rev_sample(n)
+    return {"value": flops_rev(n) / dt / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one oracle chol_unblocked_rev (plain C, OpenMP rows) at N={n} on the same SE "
+                       f"recipe (seed {SE_SEED}), {dt:.2f} s; throughput = 2N^3/3 / time")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    for _ in range(args.warmup):
+        oracle_rev_sample(n)
+    times, cores = [], 1
+    for _ in range(args.steps):
+        dt, cores = oracle_rev_sample(n)
+        times.append(dt)
+    tot = sum(times)
+    value = flops_rev(n) * args.steps / tot / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": ours_config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: one oracle chol_unblocked_rev at N={n} (same SE recipe)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_config(args):
+    return {"workload": f"chol_rev FP64 N={args.n}, SE covariance ell 0.3 on [0,1]^3 + 1e-4 I (seed {SE_SEED})",
+            "n": args.n, "nb": args.nb or "default",
+            "step": "chol_fwd -> chol_fwd_sens -> chol_rev on one N x N problem",
+            "l2": "inputs exceed L2 (512 MiB per FP64 matrix at N=8192); no flush",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# our CUDA path
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1602_07527_gb300 as cd
+    from paper_1602_07527_gb300 import workloads as W
+
+    d = Dist("nccl")
+    torch.cuda.set_device(d.local)
+    dev = torch.device("cuda", d.local)
+    n, nb = args.n, args.nb
+
+    S, Lb = W.large_se_case(n, SE_SEED)
+    Sd = W.sigma_dot(n, SE_SEED)
+    S0 = torch.tensor(np.tril(S), device=dev)
+    Lb0 = torch.tensor(Lb, device=dev)
+    Sd0 = torch.tensor(np.tril(Sd), device=dev)
+    del S, Sd
+    A = torch.empty_like(S0)
+    Ab = torch.empty_like(Lb0)
+    Ad = torch.empty_like(Sd0)
+    stream = torch.cuda.current_stream(dev)
+    cd.reserve(cd.workspace_size(n, nb), dev)
+
+    def step(prec="fp64"):
+        A.copy_(S0)
+        Ab.copy_(Lb0)
+        Ad.copy_(Sd0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        info = cd.chol_fwd(A, nb=nb, prec=prec)
+        ev[1].record(stream)
+        cd.chol_fwd_sens(A, Ad, nb=nb, prec=prec)
+        ev[2].record(stream)
+        cd.chol_rev(A, Ab, nb=nb, prec=prec)
+        ev[3].record(stream)
+        return ev, info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cd.profile_read(dev)  # discard warm-up records
+    cd.profile_enable(True, dev)
+    clocks = ClockSampler(d.local)
+    d.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = cd.launch_count(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    evs = []
+    for _ in range(args.steps):
+        evs.append(step())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    clock_info = clocks.stop()
+    launches = cd.launch_count(dev) - launches0
+    kstats = cd.profile_read(dev)
+    cd.profile_enable(False, dev)
+    total_ms = d.max(t0.elapsed_time(t1))
+    op_ms = {"chol_fwd": [], "chol_fwd_sens": [], "chol_rev": []}
+    for ev, info in evs:
+        op_ms["chol_fwd"].append(ev[0].elapsed_time(ev[1]))
+        op_ms["chol_fwd_sens"].append(ev[1].elapsed_time(ev[2]))
+        op_ms["chol_rev"].append(ev[2].elapsed_time(ev[3]))
+        if int(info.item()) != 0:
+            raise RuntimeError("factorisation reported a non-positive pivot")
+    rev_ms = d.max(statistics.median(op_ms["chol_rev"]))
+    value = d.ws * flops_rev(n) / (rev_ms * 1e-3) / 1e12
+    ops = {k: {"ms_median": statistics.median(v),
+               "tflops": {"chol_fwd": flops_fwd, "chol_fwd_sens": flops_sens, "chol_rev": flops_rev}[k](n)
+               / (statistics.median(v) * 1e-3) / 1e12} for k, v in op_ms.items()}
+
+    # roofline of the dominant kernel (largest total device time in the timed region)
+    dom = kstats[0] if kstats else None
+    roofline = None
+    if dom:
+        achieved = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 pipe)",
+                    "launches": dom["launches"], "ms_per_launch": dom["ms"] / max(1, dom["launches"]),
+                    "share_of_timed_region": dom["ms"] / (t0.elapsed_time(t1))}
+    kernels = [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 3),
+                "share": k["ms"] / t0.elapsed_time(t1),
+                "tflops": (k["flops"] / (k["ms"] * 1e-3) / 1e12) if k["ms"] > 0 else 0.0}
+               for k in kstats[:8]]
+
+    # end to end through the public call with host buffers (pinned), rev only
+    e2e = None
+    if not args.no_e2e:
+        Lh = A.cpu().pin_memory()
+        Lbh = Lb0.cpu().pin_memory()
+        outh = torch.empty_like(Lbh).pin_memory()
+        Ld = torch.empty_like(A)
+        Abd = torch.empty_like(Ab)
+
+        def e2e_step():
+            Ld.copy_(Lh, non_blocking=True)
+            Abd.copy_(Lbh, non_blocking=True)
+            cd.chol_rev(Ld, Abd, nb=nb)
+            outh.copy_(Abd, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ks = max(1, min(args.steps, 3))
+        d.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ks):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = d.max(e0.elapsed_time(e1) / ks)
+        e2e = {"value": d.ws * flops_rev(n) / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
+               "ms_per_step": e2e_ms, "path": "pinned host L, L_bar -> device -> cd_chol_rev -> host Sigma_bar"}
+
+    cpu = None
+    if d.rank == 0 and d.ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_n)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: SE covariance (ell 0.3, points U[0,1]^3, jitter 1e-4), L_bar and Sigma_dot iid N(0,1)",
+        "config": ours_config(args), "ops": ops, "roofline": roofline, "kernels": kernels,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
+        "step_tflops": d.ws * (flops_fwd(n) + flops_sens(n) + flops_rev(n)) / (total_ms / args.steps * 1e-3) / 1e12,
+    }
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

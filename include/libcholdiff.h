@@ -175,6 +175,27 @@ long long cd_launch_count(const cd_handle *h);
 /* Library version string. */
 const char *cd_version(void);
 
+/*
+ * Kernel profiler (measurement support; the paper has no counterpart).
+ * While enabled, the handle records a CUDA event pair around every kernel it
+ * launches, tagged with the kernel kind and that launch's algorithmic work
+ * (useful flops of the products it computes and the minimum bytes it must
+ * move).  cd_profile_read synchronises the handle's device, aggregates the
+ * recorded launches per kind into out[0..*count) (at most `max` kinds, in
+ * order of total time, largest first) and clears the record.  Recording
+ * costs one event pair per launch; it does not change any result.
+ */
+typedef struct {
+  char name[48];      /* kernel kind, e.g. "gemm_f64<SYM2,N>"          */
+  long long launches; /* launches recorded                              */
+  double ms;          /* sum of per-launch device time (CUDA events)    */
+  double flops;       /* sum of algorithmic flops                       */
+  double bytes;       /* sum of algorithmic bytes                       */
+} cd_kernel_stat;
+
+int cd_profile_enable(cd_handle *h, int on);
+int cd_profile_read(cd_handle *h, cd_kernel_stat *out, int max, int *count);
+
 #ifdef __cplusplus
 }
 #endif

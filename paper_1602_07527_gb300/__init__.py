@@ -8,8 +8,10 @@ continuous-batching request loop.
 """
 from .native import (CholDiffError, chol_fwd, chol_fwd_batched, chol_fwd_sens,  # noqa: F401
                      chol_fwd_sens_batched, chol_rev, chol_rev_batched, device_error,
-                     launch_count, reserve, version, workspace_size)
+                     launch_count, profile_enable, profile_read, reserve, version,
+                     workspace_size)
 
 __all__ = ["CholDiffError", "chol_fwd", "chol_fwd_batched", "chol_fwd_sens", "chol_fwd_sens_batched",
-           "chol_rev", "chol_rev_batched", "device_error", "launch_count", "reserve", "version",
+           "chol_rev", "chol_rev_batched", "device_error", "launch_count", "profile_enable", "profile_read",
+           "reserve", "version",
            "workspace_size"]

@@ -7,10 +7,12 @@
 // all still-active problems goes into one grouped launch per kernel kind, so
 // small problems share the GPU.
 #include <cuda_runtime.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "cd_internal.h"
@@ -80,6 +82,41 @@ struct Prob {
   int col0;      // global column of this (sub)problem's first column (info)
 };
 
+// Per-launch event records of cd_profile_enable.
+struct Profiler {
+  struct Rec {
+    int kind;
+    cudaEvent_t e0, e1;
+    double flops, bytes;
+  };
+  std::vector<std::string> names;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int kind_id(const char *name) {
+    for (size_t i = 0; i < names.size(); ++i)
+      if (names[i] == name) return (int)i;
+    names.emplace_back(name);
+    return (int)names.size() - 1;
+  }
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~Profiler() {
+    for (auto &r : recs) {
+      cudaEventDestroy(r.e0);
+      cudaEventDestroy(r.e1);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Ctx {
   cd_handle *h;
   cudaStream_t s;
@@ -95,7 +132,27 @@ struct Ctx {
   void cuda(cudaError_t e) {  // after any other CUDA call
     if (e != cudaSuccess && err == CD_OK) err = CD_ECUDA;
   }
+  // Launch through f(), recording an event pair around it when profiling.
+  template <class F>
+  void launch(const char *kind, double flops, double bytes, F &&f) {
+    Profiler *pr = h->prof_on ? (Profiler *)h->prof : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (pr) {
+      e0 = pr->ev();
+      e1 = pr->ev();
+      cudaEventRecord(e0, s);
+    }
+    const cudaError_t e = f();
+    if (pr) {
+      cudaEventRecord(e1, s);
+      pr->recs.push_back({pr->kind_id(kind), e0, e1, flops, bytes});
+    }
+    check(e);
+  }
 };
+
+const char *kAName[3] = {"N", "T", "SYM2"};
+const char *kBName[3] = {"N", "T", "TL"};
 
 // Accumulates GEMMs of one kind into a grouped launch.
 struct GemmBatch {
@@ -146,10 +203,22 @@ struct GemmBatch {
   }
   void flush() {
     if (g.count == 0) return;
-    c.check(launch_gemm_group(g, c.s));
+    double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
-    for (int p = 0; p < g.count; ++p) red |= g.d[p].splits > 1;
-    if (red) c.check(launch_reduce_group(g, c.s));
+    for (int p = 0; p < g.count; ++p) {
+      const GemmDesc &d = g.d[p];
+      const double outs = g.lower ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N;
+      flops += 2.0 * d.K * outs;
+      bytes += 8.0 * ((double)d.M * d.K + (double)d.K * d.N + outs * (d.beta != 0.0 ? 2.0 : 1.0));
+      if (d.splits > 1) {
+        red = true;
+        rbytes += 8.0 * outs * (d.splits + (d.beta != 0.0 ? 2.0 : 1.0));
+      }
+    }
+    char name[48];
+    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "");
+    c.launch(name, flops, bytes, [&] { return launch_gemm_group(g, c.s); });
+    if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, [&] { return launch_reduce_group(g, c.s); });
     g.count = 0;
     g.total_tiles = 0;
     part_used = 0;
@@ -169,7 +238,18 @@ struct TileBatch {
   }
   void flush() {
     if (g.count == 0) return;
-    c.check(launch_tile_group(op, g, c.s));
+    static const char *names[4] = {"tile_potf2", "tile_rev", "tile_sens", "tile_trtri"};
+    double flops = 0, bytes = 0;
+    for (int p = 0; p < g.count; ++p) {
+      const double t = g.d[p].t, tri = 0.5 * t * (t + 1) * 8.0;
+      switch (op) {
+        case T_POTF2: flops += t * t * t / 3.0 * (g.d[p].inv ? 2.0 : 1.0); bytes += 2 * tri + (g.d[p].inv ? 8 * t * t : 0); break;
+        case T_REV: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
+        case T_SENS: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
+        case T_TRTRI: flops += t * t * t / 3.0; bytes += tri + 8 * t * t; break;
+      }
+    }
+    c.launch(names[op], flops, bytes, [&] { return launch_tile_group(op, g, c.s); });
     g.count = 0;
   }
   ~TileBatch() { flush(); }
@@ -318,7 +398,9 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       const int j = s * nb;
       if (j >= p.n) continue;
       const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+      if (m > 0)
+        c.launch("copy_f64", 0.0, 16.0 * m * w,
+                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
     }
   }
 }
@@ -349,7 +431,9 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       int j, k;
       if (!blk(p, s, j, k)) continue;
       const int w = k - j, m = p.n - k;
-      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+      if (m > 0)
+        c.launch("copy_f64", 0.0, 16.0 * m * w,
+                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
     }
     {  // r2: B_bar <- B_bar - C_bar R
       GemmBatch gb(c, A_N, B_N, false);
@@ -489,7 +573,9 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       const int j = s * nb;
       if (j >= p.n) continue;
       const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0) c.check(launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s));
+      if (m > 0)
+        c.launch("copy_f64", 0.0, 16.0 * m * w,
+                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
     }
   }
 }
@@ -571,7 +657,9 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   }
   if (c.err) return c.err;
   if (op == OP_REV && opt.out == CD_OUT_SYM)
-    for (auto &p : P) c.check(launch_mirror_lower(p.X, p.ldx, p.n, s));
+    for (auto &p : P)
+      c.launch("mirror_f64", 0.0, 8.0 * p.n * (p.n - 1.0),
+               [&] { return launch_mirror_lower(p.X, p.ldx, p.n, s); });
   return c.err;
 }
 
@@ -627,6 +715,7 @@ int cd_create(cd_handle **h, int device) {
 int cd_destroy(cd_handle *h) {
   if (!h) return CD_OK;
   DeviceGuard guard(h->device);
+  delete (Profiler *)h->prof;
   if (h->ws) cudaFree(h->ws);
   if (h->dev_err) cudaFree(h->dev_err);
   free(h);
@@ -696,5 +785,45 @@ int cd_get_last_device_error(cd_handle *h, int *code) {
 }
 
 long long cd_launch_count(const cd_handle *h) { return h ? h->launches : 0; }
+
+int cd_profile_enable(cd_handle *h, int on) {
+  if (!h) return CD_EINVAL;
+  if (on && !h->prof) h->prof = new Profiler();
+  h->prof_on = on ? 1 : 0;
+  return CD_OK;
+}
+
+int cd_profile_read(cd_handle *h, cd_kernel_stat *out, int max, int *count) {
+  if (!h || !count || (max > 0 && !out)) return CD_EINVAL;
+  *count = 0;
+  Profiler *pr = (Profiler *)h->prof;
+  if (!pr) return CD_OK;
+  DeviceGuard guard(h->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return CD_ECUDA;
+  std::vector<cd_kernel_stat> agg(pr->names.size());
+  for (size_t i = 0; i < agg.size(); ++i) {
+    memset(&agg[i], 0, sizeof(cd_kernel_stat));
+    snprintf(agg[i].name, sizeof(agg[i].name), "%s", pr->names[i].c_str());
+  }
+  int rc = CD_OK;
+  for (auto &r : pr->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) rc = CD_ECUDA;
+    cd_kernel_stat &a = agg[r.kind];
+    a.launches += 1;
+    a.ms += ms;
+    a.flops += r.flops;
+    a.bytes += r.bytes;
+    pr->pool.push_back(r.e0);
+    pr->pool.push_back(r.e1);
+  }
+  pr->recs.clear();
+  std::sort(agg.begin(), agg.end(), [](const cd_kernel_stat &a, const cd_kernel_stat &b) { return a.ms > b.ms; });
+  int k = 0;
+  for (auto &a : agg)
+    if (a.launches > 0 && k < max) out[k++] = a;
+  *count = k;
+  return rc;
+}
 
 }  // extern "C"

@@ -76,6 +76,8 @@ struct cd_handle {
   size_t ws_bytes;
   int *dev_err;
   long long launches;
+  int prof_on;  // cd_profile_enable
+  void *prof;   // profiler state (cd_api.cu)
 };
 
 namespace cd {

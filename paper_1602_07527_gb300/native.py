@@ -28,6 +28,11 @@ class CholDiffError(RuntimeError):
         self.code = code
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong)]
@@ -71,6 +76,8 @@ def lib():
         L.cd_launch_count.argtypes = [_vp]
         L.cd_launch_count.restype = _ll
         L.cd_version.restype = ctypes.c_char_p
+        L.cd_profile_enable.argtypes = [_vp, _i]
+        L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
         _lib = L
     return _lib
 
@@ -80,7 +87,7 @@ def exported_symbols():
     return ["cd_create", "cd_destroy", "cd_options_default", "cd_workspace_size", "cd_reserve",
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
-            "cd_launch_count", "cd_version"]
+            "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read"]
 
 
 def handle(device=None):
@@ -243,6 +250,20 @@ def workspace_size(n, nb=0, prec="fp64", device=None):
 
 def reserve(nbytes, device=None):
     _check(lib().cd_reserve(handle(device), int(nbytes)), "cd_reserve")
+
+
+def profile_enable(on=True, device=None):
+    """Record a CUDA event pair around every library kernel launch (see profile_read)."""
+    _check(lib().cd_profile_enable(handle(device), 1 if on else 0), "cd_profile_enable")
+
+
+def profile_read(device=None, max_kinds=64):
+    """Synchronise, aggregate and clear the recorded launches: list of dicts per kernel kind."""
+    arr = (KernelStat * max_kinds)()
+    cnt = _i()
+    _check(lib().cd_profile_read(handle(device), arr, max_kinds, ctypes.byref(cnt)), "cd_profile_read")
+    return [dict(name=arr[k].name.decode(), launches=int(arr[k].launches), ms=float(arr[k].ms),
+                 flops=float(arr[k].flops), bytes=float(arr[k].bytes)) for k in range(cnt.value)]
 
 
 def version():
