@@ -77,6 +77,7 @@ extern "C" {
 #define CD_ENOMEM (-2)   /* workspace allocation failed                           */
 #define CD_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed          */
 #define CD_ETIMEOUT (-4) /* device word: a bounded device-side wait ran out       */
+#define CD_ESCRATCH (-5) /* cd_chol_rev_noalloc: problem larger than its fixed scratch */
 
 typedef enum {
   CD_FP64 = 0,          /* all FP64 (DFMA)                                    */
@@ -163,6 +164,43 @@ int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *con
 int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L,
                              const long long *ldl, double *const *Adot, const long long *lda,
                              const cd_options *opt, void *stream);
+
+/*
+ * Reverse mode without any allocation (no counterpart in the paper: this is a
+ * service for callers, not a step of the method).
+ *
+ * Some callers cannot allocate device memory when they need the gradient:
+ * code running inside a region whose allocations are forbidden (a custom
+ * allocator's callbacks, a framework that owns all device memory), or an
+ * embedding that must never let the library grow its footprint.  They cannot
+ * use cd_chol_rev, whose handle allocates its workspace on demand, nor even
+ * cd_create.  This entry point computes the same result as cd_chol_rev with
+ * CD_FP64 for one problem, with no handle: all of its scratch (inverses of
+ * L's diagonal blocks, the solved panel, split-K partial sums) lives in one
+ * fixed 8 MiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.  The call performs no cudaMalloc,
+ * cudaFree or other allocating call.
+ *
+ *   n       problem size, 0 <= n <= CD_NOALLOC_MAX_N (2048); larger n returns
+ *           CD_ESCRATCH and does nothing.
+ *   L, ldl  device factor as for cd_chol_rev; Abar, lda in/out as for cd_chol_rev.
+ *   nb      block size, 0 (default) or 1..CD_NOALLOC_MAX_NB (128).
+ *   out     CD_OUT_TRIL or CD_OUT_SYM.
+ *   stream  cudaStream_t of the call; runs on the current CUDA device.
+ *
+ * The first call on a device looks up the array's device address and
+ * prepares the kernels (no allocation); make that first call before any
+ * stream capture.  Every call on a device shares the one array and each call
+ * leaves its contents behind; no word of it needs to start at zero, since a
+ * call writes every scratch word before reading it.  Calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * the array and give wrong results: order them.  Results agree with
+ * cd_chol_rev to rounding (the split-K partition may differ).
+ */
+#define CD_NOALLOC_MAX_N 2048
+#define CD_NOALLOC_MAX_NB 128
+int cd_chol_rev_noalloc(int n, const double *L, long long ldl, double *Abar, long long lda,
+                        int nb, int out, void *stream);
 
 /* Read and clear the handle's device error word (synchronises the handle's
  * device).  *code receives CD_OK or a negative CD_* code. */

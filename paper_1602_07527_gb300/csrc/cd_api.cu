@@ -667,6 +667,45 @@ bool g_init_done = false;
 
 }  // namespace
 
+namespace cd {
+
+// Workspace bytes the reverse pass needs for one problem of size n with block
+// size nb when nb <= kTileMax (inverse blocks and the solved panel; split-K
+// partial sums use whatever is left and are optional).
+size_t rev_scratch_need(int n, int nb) { return prob_bytes(n, nb) + 2 * kAlign; }
+
+// The reverse pass of one problem with every scratch word taken from the
+// given device block instead of the handle's workspace.  Used by
+// cd_chol_rev_noalloc; performs no allocation.  nb must be <= kTileMax.
+int rev_in_scratch(int n, const double *L, long long ldl, double *Abar, long long lda, int nb, int out,
+                   void *scratch, size_t scratch_bytes, int num_sms, cudaStream_t s) {
+  cd_handle hh;
+  memset(&hh, 0, sizeof(hh));
+  cudaGetDevice(&hh.device);
+  hh.num_sms = num_sms;
+  Arena ar;
+  ar.base = (char *)scratch;
+  ar.cap = scratch_bytes;
+  cd_options opt;
+  cd_options_default(&opt);
+  opt.nb = nb;
+  opt.out = out;
+  std::vector<Prob> P(1);
+  P[0] = Prob{n, L, ldl, Abar, lda, nullptr, nullptr, nullptr, 0};
+  if (!bind_workspace(P, nb, ar)) return CD_EINVAL;
+  Ctx c{&hh, s, &opt, nullptr, 0, 2 * num_sms};
+  const size_t left = ar.cap > align_up(ar.off) ? ar.cap - align_up(ar.off) : 0;
+  c.part_cap = left / sizeof(double);
+  c.part = c.part_cap ? (double *)ar.take(c.part_cap * sizeof(double)) : nullptr;
+  if (!c.part) c.part_cap = 0;
+  run_rev(c, P, nb, ar);
+  if (c.err) return c.err;
+  if (out == CD_OUT_SYM) c.check(launch_mirror_lower(Abar, lda, n, s));
+  return c.err;
+}
+
+}  // namespace cd
+
 extern "C" {
 
 const char *cd_version(void) { return "libcholdiff 0.1 (sm_103a)"; }

@@ -15,9 +15,10 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcholdiff.so")
 
-CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT = 0, -1, -2, -3, -4
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_ESCRATCH = 0, -1, -2, -3, -4, -5
 _ERR = {CD_EINVAL: "invalid argument", CD_ENOMEM: "workspace allocation failed",
-        CD_ECUDA: "CUDA error", CD_ETIMEOUT: "device-side wait timed out"}
+        CD_ECUDA: "CUDA error", CD_ETIMEOUT: "device-side wait timed out",
+        CD_ESCRATCH: "problem larger than the fixed scratch of cd_chol_rev_noalloc"}
 PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
 OUT = {"tril": 0, "sym": 1}
 
@@ -78,6 +79,7 @@ def lib():
         L.cd_version.restype = ctypes.c_char_p
         L.cd_profile_enable.argtypes = [_vp, _i]
         L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
+        L.cd_chol_rev_noalloc.argtypes = [_i, _vp, _ll, _vp, _ll, _i, _i, _vp]
         _lib = L
     return _lib
 
@@ -87,7 +89,8 @@ def exported_symbols():
     return ["cd_create", "cd_destroy", "cd_options_default", "cd_workspace_size", "cd_reserve",
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
-            "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read"]
+            "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
+            "cd_chol_rev_noalloc"]
 
 
 def handle(device=None):
