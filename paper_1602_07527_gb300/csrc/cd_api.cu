@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kDefaultNbSmall = 64;
 constexpr int kDefaultNbLarge = 128;
-constexpr size_t kPartBytes = size_t(64) << 20;  // split-K partial sums
+constexpr size_t kPartBytes = size_t(64) << 20;  // split-K partial sums, per stream
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -125,6 +125,9 @@ struct Ctx {
   size_t part_cap;  // doubles
   int target_ctas;
   int err = CD_OK;
+  cudaStream_t side = nullptr;  // second stream (null: everything on s)
+  double *part2 = nullptr;      // split-K partials of work on the side stream
+  size_t part2_cap = 0;
   void check(cudaError_t e) {  // after a kernel launch
     ++h->launches;
     cuda(e);
@@ -134,94 +137,146 @@ struct Ctx {
   }
   // Launch through f(), recording an event pair around it when profiling.
   template <class F>
-  void launch(const char *kind, double flops, double bytes, F &&f) {
+  void launch(const char *kind, double flops, double bytes, cudaStream_t st, F &&f) {
     Profiler *pr = h->prof_on ? (Profiler *)h->prof : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (pr) {
       e0 = pr->ev();
       e1 = pr->ev();
-      cudaEventRecord(e0, s);
+      cudaEventRecord(e0, st);
     }
     const cudaError_t e = f();
     if (pr) {
-      cudaEventRecord(e1, s);
+      cudaEventRecord(e1, st);
       pr->recs.push_back({pr->kind_id(kind), e0, e1, flops, bytes});
     }
     check(e);
+  }
+  template <class F>
+  void launch(const char *kind, double flops, double bytes, F &&f) {
+    launch(kind, flops, bytes, s, f);
+  }
+  // Work enqueued on side() after fork() may run concurrently with work on s
+  // until join() makes s wait for it.
+  void fork() {
+    if (!side) return;
+    cuda(cudaEventRecord(h->ev_fork, s));
+    cuda(cudaStreamWaitEvent(side, h->ev_fork, 0));
+  }
+  void join() {
+    if (!side) return;
+    cuda(cudaEventRecord(h->ev_join, side));
+    cuda(cudaStreamWaitEvent(s, h->ev_join, 0));
   }
 };
 
 const char *kAName[3] = {"N", "T", "SYM2"};
 const char *kBName[3] = {"N", "T", "TL"};
 
-// Accumulates GEMMs of one kind into a grouped launch.
+// Accumulates GEMMs of one kind into a grouped launch.  The split-K factor
+// is chosen at flush time for the whole group so that the grid fills whole
+// waves of resident CTAs (c.target_ctas), which keeps every SM's FP64 pipe
+// busy to the end of the launch.
 struct GemmBatch {
   Ctx &c;
   GemmGroup g;
-  size_t part_used = 0;
-  GemmBatch(Ctx &ctx, int amode, int bmode, bool lower) : c(ctx) {
+  cudaStream_t st;
+  double *part;
+  size_t part_cap;
+  GemmBatch(Ctx &ctx, int amode, int bmode, bool lower, bool on_side = false) : c(ctx) {
     memset(&g, 0, sizeof(g));
     g.amode = amode;
     g.bmode = bmode;
     g.lower = lower ? 1 : 0;
+    const bool side = on_side && c.side;
+    st = side ? c.side : c.s;
+    part = side ? c.part2 : c.part;
+    part_cap = side ? c.part2_cap : c.part_cap;
   }
   void add(int M, int N, int K, const double *A, long long lda, const double *B, long long ldb, const double *Cin,
            long long ldcin, double *Cout, long long ldcout, double alpha, double beta) {
     if (M <= 0 || N <= 0) return;
     if (K <= 0 && beta == 1.0 && Cin == Cout && ldcin == ldcout) return;  // identity update
-    const int tm = (M + 63) / 64, tn = (N + 63) / 64;
-    const int tiles_eff = g.lower ? std::max(1, tm * (tm + 1) / 2) : tm * tn;
-    int splits = 1;
-    if (K > 0 && tiles_eff < c.target_ctas) {
-      splits = (c.target_ctas + tiles_eff - 1) / tiles_eff;
-      splits = std::min(splits, std::max(1, K / 256));
-      splits = std::min(splits, 64);
-    }
-    const size_t mn = (size_t)M * N;
-    if (splits > 1 && mn * splits > c.part_cap) splits = (int)std::max<size_t>(1, c.part_cap / mn);
-    if (splits > 1 && part_used + mn * splits > c.part_cap) flush();
-    int kchunk = std::max(K, 1);
-    if (splits > 1) {
-      kchunk = (K + splits - 1) / splits;
-      kchunk = (kchunk + 15) / 16 * 16;
-      splits = (K + kchunk - 1) / kchunk;
-    }
     if (g.count == kMaxGemm) flush();
     GemmDesc &d = g.d[g.count++];
     d.A = A; d.B = B; d.Cin = Cin; d.Cout = Cout;
     d.lda = lda; d.ldb = ldb; d.ldcin = ldcin; d.ldcout = ldcout;
     d.alpha = alpha; d.beta = beta;
-    d.M = M; d.N = N; d.K = K; d.splits = splits; d.kchunk = kchunk;
-    d.tiles_m = tm; d.tiles_n = tn;
-    d.tile_begin = g.total_tiles;
+    d.M = M; d.N = N; d.K = K; d.splits = 1; d.kchunk = std::max(K, 1);
+    d.tiles_m = (M + 63) / 64;
+    d.tiles_n = (N + 63) / 64;
     d.part = nullptr;
-    if (splits > 1) {
-      d.part = c.part + part_used;
-      part_used += mn * splits;
+  }
+  int per_split(const GemmDesc &d) const { return g.lower ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n; }
+  static double wave_eff(long long ctas, int slots) {
+    const long long waves = (ctas + slots - 1) / slots;
+    return (double)ctas / (double)(waves * slots);
+  }
+  int choose_splits() const {
+    const int slots = std::max(1, c.target_ctas);
+    long long t1 = 0;
+    int smax = 1;
+    for (int p = 0; p < g.count; ++p) {
+      t1 += per_split(g.d[p]);
+      smax = std::max(smax, g.d[p].K / 16);
     }
-    g.total_tiles += tm * tn * splits;
+    if (t1 >= 4LL * slots) return 1;
+    smax = std::min(smax, 64);
+    int best = 1;
+    double best_e = wave_eff(t1, slots);
+    for (int s2 = 2; s2 <= smax && best_e < 0.9; ++s2) {
+      const double e = wave_eff(t1 * s2, slots);
+      if (e >= 0.9) return s2;
+      if (e > best_e + 0.02) {
+        best = s2;
+        best_e = e;
+      }
+    }
+    return best;
   }
   void flush() {
     if (g.count == 0) return;
+    const int sg = choose_splits();
+    size_t used = 0;
+    int tiles = 0;
     double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
     for (int p = 0; p < g.count; ++p) {
-      const GemmDesc &d = g.d[p];
+      GemmDesc &d = g.d[p];
+      int sp = std::min(sg, std::max(1, d.K / 16));
+      int kchunk = std::max(d.K, 1);
+      if (sp > 1) {
+        kchunk = ((d.K + sp - 1) / sp + 15) / 16 * 16;
+        sp = (d.K + kchunk - 1) / kchunk;
+      }
+      const size_t mn = (size_t)d.M * d.N;
+      d.part = nullptr;
+      if (sp > 1 && part && used + mn * sp <= part_cap) {
+        d.part = part + used;
+        used += mn * sp;
+      } else {
+        sp = 1;
+        kchunk = std::max(d.K, 1);
+      }
+      d.splits = sp;
+      d.kchunk = kchunk;
+      d.tile_begin = tiles;
+      tiles += per_split(d) * sp;
       const double outs = g.lower ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N;
       flops += 2.0 * d.K * outs;
       bytes += 8.0 * ((double)d.M * d.K + (double)d.K * d.N + outs * (d.beta != 0.0 ? 2.0 : 1.0));
-      if (d.splits > 1) {
+      if (sp > 1) {
         red = true;
-        rbytes += 8.0 * outs * (d.splits + (d.beta != 0.0 ? 2.0 : 1.0));
+        rbytes += 8.0 * outs * (sp + (d.beta != 0.0 ? 2.0 : 1.0));
       }
     }
+    g.total_tiles = tiles;
     char name[48];
     snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "");
-    c.launch(name, flops, bytes, [&] { return launch_gemm_group(g, c.s); });
-    if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, [&] { return launch_reduce_group(g, c.s); });
+    c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(g, st); });
+    if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(g, st); });
     g.count = 0;
     g.total_tiles = 0;
-    part_used = 0;
   }
   ~GemmBatch() { flush(); }
 };
@@ -343,6 +398,18 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();  // f3 does not depend on f1 / f2 of this step
+    {  // f3: C <- C - B R^T
+      GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j;
+        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.X + (long long)j * p.ldx, p.ldx, C, p.ldx, C, p.ldx,
+               -1.0, 1.0);
+      }
+    }
     {  // f1: D <- D - tril(R R^T)
       GemmBatch gb(c, A_N, B_T, true);
       for (auto &p : P) {
@@ -374,17 +441,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         }
       }
     }
-    {  // f3: C <- C - B R^T
-      GemmBatch gb(c, A_N, B_T, false);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *C = p.X + (long long)k * p.ldx + j;
-        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.X + (long long)j * p.ldx, p.ldx, C, p.ldx, C, p.ldx,
-               -1.0, 1.0);
-      }
-    }
+    c.join();
     {  // f4: C <- C tril(D)^{-T}   (W = C Dinv^T, then copy back)
       GemmBatch gb(c, A_N, B_T, false);
       for (auto &p : P) {
@@ -435,8 +492,9 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         c.launch("copy_f64", 0.0, 16.0 * m * w,
                  [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
     }
+    c.fork();  // r2 writes B_bar only; r3, r4, r5 neither read nor write it
     {  // r2: B_bar <- B_bar - C_bar R
-      GemmBatch gb(c, A_N, B_N, false);
+      GemmBatch gb(c, A_N, B_N, false, /*on_side=*/true);
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -487,6 +545,7 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                Rb, p.ldx, -1.0, 1.0);
       }
     }
+    c.join();  // the next step's panel was written by r2 and r5
   }
 }
 
@@ -497,6 +556,22 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();  // g3 does not depend on g1 / g2 of this step
+    for (int term = 0; term < 2; ++term) {  // g3: C_dot <- C_dot - B_dot R^T - B R_dot^T
+      GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *Cd = p.X + (long long)k * p.ldx + j;
+        if (term == 0)
+          gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Cd, p.ldx, Cd,
+                 p.ldx, -1.0, 1.0);
+        else
+          gb.add(m, w, j, p.L + (long long)k * p.ldl, p.ldl, p.X + (long long)j * p.ldx, p.ldx, Cd, p.ldx, Cd,
+                 p.ldx, -1.0, 1.0);
+      }
+    }
     for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
       GemmBatch gb(c, A_N, B_T, true);
       for (auto &p : P) {
@@ -533,21 +608,7 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         }
       }
     }
-    for (int term = 0; term < 2; ++term) {  // g3: C_dot <- C_dot - B_dot R^T - B R_dot^T
-      GemmBatch gb(c, A_N, B_T, false);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cd = p.X + (long long)k * p.ldx + j;
-        if (term == 0)
-          gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Cd, p.ldx, Cd,
-                 p.ldx, -1.0, 1.0);
-        else
-          gb.add(m, w, j, p.L + (long long)k * p.ldl, p.ldl, p.X + (long long)j * p.ldx, p.ldx, Cd, p.ldx, Cd,
-                 p.ldx, -1.0, 1.0);
-      }
-    }
+    c.join();
     {  // g4a: C_dot <- C_dot - C D_dot^T
       GemmBatch gb(c, A_N, B_TL, false);
       for (auto &p : P) {
@@ -583,7 +644,7 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 enum Op { OP_FWD, OP_REV, OP_SENS };
 
 size_t need_bytes(const int *n, int batch, int nb) {
-  size_t b = kPartBytes + recursion_bytes(nb) + kAlign;
+  size_t b = 2 * kPartBytes + recursion_bytes(nb) + 2 * kAlign;
   for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb) + 2 * kAlign;
   return b;
 }
@@ -637,9 +698,12 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   Arena ar;
   ar.base = (char *)h->ws;
   ar.cap = h->ws_bytes;
-  Ctx c{h, s, &opt, nullptr, 0, 2 * h->num_sms};
+  Ctx c{h, s, &opt, nullptr, 0, h->gemm_slots};
   c.part = (double *)ar.take(kPartBytes);
   c.part_cap = kPartBytes / sizeof(double);
+  c.side = h->side;
+  c.part2 = (double *)ar.take(kPartBytes);
+  c.part2_cap = kPartBytes / sizeof(double);
   std::vector<Prob> P;
   P.reserve(batch);
   for (int b = 0; b < batch; ++b) {
@@ -650,10 +714,25 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   }
   if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
   if (opt.prec != CD_FP64 && !mixed_available()) return CD_EINVAL;
+  // The step loops issue the diagonal chain on the high-priority stream (its
+  // CTAs are scheduled first when SM slots free up) and the independent bulk
+  // GEMM of each step on the side stream; both start after, and the caller's
+  // stream resumes after, all of it.
+  if (h->crit) {
+    c.cuda(cudaEventRecord(h->ev_in, s));
+    c.cuda(cudaStreamWaitEvent(h->crit, h->ev_in, 0));
+    c.s = h->crit;
+  }
   switch (op) {
     case OP_FWD: run_fwd(c, P, nb, ar); break;
     case OP_REV: run_rev(c, P, nb, ar); break;
     case OP_SENS: run_sens(c, P, nb, ar); break;
+  }
+  if (h->crit) {
+    c.join();
+    c.cuda(cudaEventRecord(h->ev_out, h->crit));
+    c.cuda(cudaStreamWaitEvent(s, h->ev_out, 0));
+    c.s = s;
   }
   if (c.err) return c.err;
   if (op == OP_REV && opt.out == CD_OUT_SYM)
@@ -747,6 +826,19 @@ int cd_create(cd_handle **h, int device) {
     free(x);
     return CD_ECUDA;
   }
+  x->gemm_slots = gemm_ctas_per_sm() * x->num_sms;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&x->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&x->crit, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(x->dev_err);
+    free(x);
+    return CD_ECUDA;
+  }
   *h = x;
   return CD_OK;
 }
@@ -757,6 +849,12 @@ int cd_destroy(cd_handle *h) {
   delete (Profiler *)h->prof;
   if (h->ws) cudaFree(h->ws);
   if (h->dev_err) cudaFree(h->dev_err);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->crit) cudaStreamDestroy(h->crit);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   free(h);
   return CD_OK;
 }

@@ -9,6 +9,8 @@
 // DFMA kernel: its only job is to keep the FP64 pipe of every SM busy.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "cd_internal.h"
 
 namespace cd {
@@ -45,11 +47,21 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
   const GemmDesc &d = g.d[p];
   const int M = d.M, N = d.N;
   const int local = bid - d.tile_begin;
-  const int per_split = d.tiles_m * d.tiles_n;
+  // tril outputs (M == N) enumerate only the tm (tm + 1) / 2 tiles on or below the diagonal
+  const int per_split = LOWER ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
   const int z = local / per_split;
   const int rem = local - z * per_split;
-  const int m0 = (rem / d.tiles_n) * GBM, n0 = (rem % d.tiles_n) * GBN;
-  if (LOWER && n0 > m0 + GBM - 1) return;  // tile entirely above the diagonal
+  int m0, n0;
+  if (LOWER) {
+    int ti = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
+    while (ti * (ti + 1) / 2 > rem) --ti;
+    m0 = ti * GBM;
+    n0 = (rem - ti * (ti + 1) / 2) * GBN;
+  } else {
+    m0 = (rem / d.tiles_n) * GBM;
+    n0 = (rem % d.tiles_n) * GBN;
+  }
   const int kbeg = z * d.kchunk;
   const int kend = min(d.K, kbeg + d.kchunk);
   const double *__restrict__ A = d.A;
@@ -154,6 +166,13 @@ cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s) {
     case A_SYM2 * 3 + B_N: return launch_gemm_ab<A_SYM2, B_N>(g, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+int gemm_ctas_per_sm() {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false>, GT, 0) != cudaSuccess) a = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false>, GT, 0) != cudaSuccess) b = 1;
+  return std::max(1, std::min(a, b));
 }
 
 cudaError_t launch_reduce_group(const GemmGroup &g, cudaStream_t s) {

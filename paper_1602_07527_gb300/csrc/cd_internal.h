@@ -78,6 +78,10 @@ struct cd_handle {
   long long launches;
   int prof_on;  // cd_profile_enable
   void *prof;   // profiler state (cd_api.cu)
+  int gemm_slots;              // resident FP64 GEMM CTAs on the whole GPU
+  cudaStream_t side;           // second stream for work independent of the diagonal chain
+  cudaStream_t crit;           // high-priority stream for the diagonal (critical) chain
+  cudaEvent_t ev_fork, ev_join, ev_in, ev_out;
 };
 
 namespace cd {
@@ -89,4 +93,5 @@ cudaError_t launch_copy(const double *src, long long lds, double *dst, long long
                         int cols, cudaStream_t s);
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
 cudaError_t tile_kernels_init();
+int gemm_ctas_per_sm();  // resident CTAs of the FP64 GEMM per SM
 }  // namespace cd
