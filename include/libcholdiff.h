@@ -202,6 +202,17 @@ int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double
 int cd_chol_rev_noalloc(int n, const double *L, long long ldl, double *Abar, long long lda,
                         int nb, int out, void *stream);
 
+/*
+ * Diagnostic: the split-BF16 tensor-core product used by the CD_MIXED_*
+ * paths, exposed so that it can be tested alone (no counterpart in the
+ * paper).  C (M x N, ldc) = A B^T with A (M x K, lda) and B (N x K, ldb), all
+ * FP64 row-major device matrices; prec is CD_MIXED_BF16X3 or
+ * CD_MIXED_BF16X6; lower != 0 (requires M == N) writes only i >= j.
+ * Uses the handle's workspace; asynchronous on stream.
+ */
+int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
+                        long long ldb, double *C, long long ldc, int prec, int lower, void *stream);
+
 /* Read and clear the handle's device error word (synchronises the handle's
  * device).  *code receives CD_OK or a negative CD_* code. */
 int cd_get_last_device_error(cd_handle *h, int *code);

@@ -52,8 +52,10 @@ struct Arena {
 };
 
 int pick_nb(int n, const cd_options *opt) {
-  if (opt && opt->nb > 0) return opt->nb;
-  return n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall;
+  int nb = (opt && opt->nb > 0) ? opt->nb : (n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall);
+  // the tensor-core path works on 64-wide K blocks: round its block size up
+  if (opt && opt->prec != CD_FP64) nb = (nb + 63) / 64 * 64;
+  return nb;
 }
 
 int nblocks(int n, int nb) { return (n + nb - 1) / nb; }
@@ -80,6 +82,11 @@ struct Prob {
   double *dinv;  // nblocks * nb * nb (ld nb)
   double *W;     // n * nb (ld nb)
   int col0;      // global column of this (sub)problem's first column (info)
+  struct Mix {    // split-BF16 term arrays of the mixed path (null in FP64)
+    void *big, *big2, *P1, *P2, *P3, *P4;
+    long long ldb, ldn;
+    int pad, T;
+  } mx;
 };
 
 // Per-launch event records of cd_profile_enable.
@@ -641,6 +648,456 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   }
 }
 
+
+// ============================================================================
+// Mixed precision: the large off-diagonal products on the tensor cores with
+// split-BF16 operands (cd_mixed.cu); diagonal tiles, their inverses and the
+// Phi / halving steps stay in FP64 (the kernels above).
+// ============================================================================
+constexpr int kMixMaxChunk = 2048;  // longest FP32 accumulation before an FP64 reduction
+
+MOp mop(void *base, long long ld, long long rows, int T, int x0, int y0) {
+  MOp o;
+  o.base = base;
+  o.ld = ld;
+  o.rows = rows;
+  o.T = T;
+  o.x0 = x0;
+  o.y0 = y0;
+  return o;
+}
+
+void split(Ctx &c, cudaStream_t st, const double *src, long long lds, int rows, int cols, int mode, int transpose,
+           void *dst, long long ldd, long long dst_rows, int reg_r0, int reg_c0, int h, int w, int dst_r0, int dst_c0,
+           int T) {
+  if (h <= 0 || w <= 0) return;
+  SplitArgs a;
+  a.src = src; a.lds = lds; a.rows = rows; a.cols = cols; a.mode = mode; a.transpose = transpose;
+  a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
+  a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
+  a.T = T;
+  c.launch("split_bf16", 0.0, (8.0 + 2.0 * T) * h * w, st, [&] { return mixed_split_launch(a, st); });
+}
+
+// Accumulates tensor-core products of one kind into grouped launches.
+struct MixedBatch {
+  Ctx &c;
+  int T;
+  bool lower;
+  cudaStream_t st;
+  double *part;
+  size_t part_cap;
+  static constexpr int kCap = 40;
+  MProblem v[kCap];
+  int count = 0;
+  MixedBatch(Ctx &ctx, int T_, bool lower_, bool on_side = false) : c(ctx), T(T_), lower(lower_) {
+    const bool side = on_side && c.side;
+    st = side ? c.side : c.s;
+    part = side ? c.part2 : c.part;
+    part_cap = side ? c.part2_cap : c.part_cap;
+  }
+  void add(const MOp &A, const MOp &B, int M, int N, int K, const double *Cin, long long ldcin, double *Cout,
+           long long ldcout, double alpha, double beta) {
+    if (M <= 0 || N <= 0 || K <= 0) return;
+    if (count == kCap) flush();
+    MProblem &P = v[count++];
+    P.A = A; P.B = B; P.M = M; P.N = N; P.K = K;
+    P.Cin = Cin; P.ldcin = ldcin; P.Cout = Cout; P.ldcout = ldcout;
+    P.alpha = alpha; P.beta = beta; P.part = nullptr; P.splits = 1; P.kchunk = (K + 63) / 64 * 64;
+  }
+  static double wave_eff(long long ctas, int slots) {
+    const long long waves = (ctas + slots - 1) / slots;
+    return (double)ctas / (double)(waves * slots);
+  }
+  void flush() {
+    if (count == 0) return;
+    const int slots = std::max(1, c.h->num_sms * mixed_ctas_per_sm());
+    long long t1 = 0;
+    int smax = 1;
+    for (int i = 0; i < count; ++i) {
+      const int tm = (v[i].M + 127) / 128, tn = (v[i].N + 127) / 128;
+      t1 += lower ? tm * (tm + 1) / 2 : tm * tn;
+      smax = std::max(smax, (v[i].K + 63) / 64);
+    }
+    int sg = 1;
+    if (t1 < 4LL * slots) {
+      double best = wave_eff(t1, slots);
+      for (int s2 = 2; s2 <= std::min(smax, 64) && best < 0.9; ++s2) {
+        const double e = wave_eff(t1 * s2, slots);
+        if (e > best + 0.02) { sg = s2; best = e; }
+      }
+    }
+    size_t used = 0;
+    double flops = 0, bytes = 0;
+    const int prods = T == 3 ? 6 : 3;
+    for (int i = 0; i < count; ++i) {
+      MProblem &P = v[i];
+      const int kblocks = (P.K + 63) / 64;
+      int sp = std::max((P.K + kMixMaxChunk - 1) / kMixMaxChunk, std::min(sg, kblocks));
+      int kchunk = ((kblocks + sp - 1) / sp) * 64;
+      sp = (P.K + kchunk - 1) / kchunk;
+      const size_t mn = (size_t)P.M * P.N;
+      if (sp > 1 && part && used + mn * sp <= part_cap) {
+        P.part = part + used;
+        used += mn * sp;
+      } else {
+        sp = 1;
+        kchunk = kblocks * 64;
+        P.part = nullptr;
+      }
+      P.splits = sp;
+      P.kchunk = kchunk;
+      const double outs = lower ? 0.5 * P.M * (P.M + 1.0) : (double)P.M * P.N;
+      flops += 2.0 * prods * P.K * outs;  // tensor-core flops (all term products)
+      bytes += 2.0 * T * ((double)P.M * P.K + (double)P.N * P.K) + outs * 8.0 * (P.beta != 0.0 ? 2.0 : 1.0);
+    }
+    char name[48];
+    snprintf(name, sizeof(name), "mgemm_bf16x%d%s", prods, lower ? "_tril" : "");
+    c.launch(name, flops, bytes, st, [&] {
+      int l = 0;
+      cudaError_t e = mixed_gemm_launch(v, count, T, lower, c.h->dev_err, st, &l);
+      if (l > 1) c.h->launches += l - 1;
+      return e;
+    });
+    count = 0;
+  }
+  ~MixedBatch() { flush(); }
+};
+
+int mix_terms(int prec) { return prec == CD_MIXED_BF16X6 ? 3 : 2; }
+
+size_t mix_bytes(int n, int nb, int T, bool two_big) {
+  if (n <= 0) return 0;
+  const size_t ldb = (size_t)((n + 8 + 63) / 64 * 64), ldn = (size_t)((n + 63) / 64 * 64 + 64);
+  const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + (size_t)nb * nb;
+  return 2 * (size_t)T * e + 8 * kAlign;
+}
+
+bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar) {
+  for (auto &p : P) {
+    memset(&p.mx, 0, sizeof(p.mx));
+    if (p.n <= 0) continue;
+    const long long n = p.n;
+    p.mx.T = T;
+    p.mx.ldb = (n + 8 + 63) / 64 * 64;
+    p.mx.ldn = (n + 63) / 64 * 64 + 64;
+    p.mx.pad = (int)((8 - n % 8) % 8);
+    const size_t t = 2 * (size_t)T;
+    p.mx.big = ar.take(t * n * p.mx.ldb);
+    p.mx.big2 = two_big ? ar.take(t * n * p.mx.ldb) : nullptr;
+    p.mx.P1 = ar.take(t * n * nb);
+    p.mx.P2 = ar.take(t * nb * p.mx.ldn);
+    p.mx.P3 = ar.take(t * nb * p.mx.ldn);
+    p.mx.P4 = ar.take(t * nb * nb);
+    if (!p.mx.big || (two_big && !p.mx.big2) || !p.mx.P1 || !p.mx.P2 || !p.mx.P3 || !p.mx.P4) return false;
+  }
+  return true;
+}
+
+// chol_blocked_rev (Sec. 4.2), products in split BF16.  L^T is split once
+// (columns shifted by pad so that every block boundary is a multiple of 8).
+void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  precompute_dinv(c, P, nb, true, ar);
+  for (auto &p : P) {
+    const auto &x = p.mx;
+    split(c, c.s, p.L, p.ldl, p.n, p.n, 1, 1, x.big, x.ldb, p.n, 0, 0, p.n, (int)x.ldb, 0, x.pad, x.T);
+  }
+  const int T = P.empty() ? 2 : P[0].mx.T;
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  auto blk = [&](const Prob &p, int s, int &j, int &k) {
+    k = p.n - s * nb;
+    j = std::max(0, k - nb);
+    return k > 0;
+  };
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    {  // r1: W = C_bar D^{-1}; W -> C_bar; W and W^T split for r2, r3
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        split(c, c.s, p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 1, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+               0.0);
+      }
+    }
+    for (auto &p : P) {
+      int j, k;
+      if (!blk(p, s, j, k)) continue;
+      const int w = k - j, m = p.n - k;
+      if (m <= 0) continue;
+      c.launch("copy_f64", 0.0, 16.0 * m * w,
+               [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+      split(c, c.s, p.W, nb, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+      split(c, c.s, p.W, nb, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, (int)p.mx.ldn, 0, 0, T);
+    }
+    c.fork();
+    {  // r2 (side stream): B_bar <- B_bar - C_bar R
+      MixedBatch mb(c, T, false, /*on_side=*/true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Bb = p.X + (long long)k * p.ldx;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), m, j, w, Bb, p.ldx,
+               Bb, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // r3: D_bar <- tril(D_bar) - tril(C_bar^T C)
+      MixedBatch mb(c, T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Db = p.X + (long long)j * p.ldx + j;
+        mb.add(mop(p.mx.P2, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, k + p.mx.pad, j), w, w, m, Db,
+               p.ldx, Db, p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)   (FP64)
+      TileBatch tb(c, T_REV);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        const double *D = p.L + (long long)j * p.ldl + j;
+        double *Db = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(D, p.ldl, Db, p.ldx, nullptr, 0, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, D, p.ldl, Db, p.ldx, nullptr, nullptr, nullptr, 0};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_rev(c, sub, kTileMax, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    {  // r5: R_bar <- R_bar - G L[j:n, 0:j],  G = [D_bar + D_bar^T, C_bar^T]
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || j == 0) continue;
+        const int w = k - j;
+        split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, w, p.n - j, 2, 0, p.mx.P3, p.mx.ldn, nb, 0, 0, w,
+              (int)p.mx.ldn, 0, 0, T);
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || j == 0) continue;
+        const int w = k - j;
+        double *Rb = p.X + (long long)j * p.ldx;
+        mb.add(mop(p.mx.P3, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), w, j, p.n - j,
+               Rb, p.ldx, Rb, p.ldx, -1.0, 1.0);
+      }
+    }
+    c.join();
+  }
+}
+
+// chol_blocked (Sec. 4.2), products in split BF16; the finished columns of L
+// are split into `big` block column by block column.
+void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  const int T = P.empty() ? 2 : P[0].mx.T;
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();
+    {  // f3 (side stream): C <- C - B R^T
+      MixedBatch mb(c, T, false, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), m, w, j, C, p.ldx, C,
+               p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // f1: D <- D - tril(R R^T)
+      MixedBatch mb(c, T, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, D, p.ldx, D,
+               p.ldx, -1.0, 1.0);
+      }
+    }
+    {  // f2: D <- chol_unblocked(D) and D^{-1}   (FP64)
+      TileBatch tb(c, T_POTF2);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(nullptr, 0, D, p.ldx, p.dinv, nb, w, p.info, p.col0 + j));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_fwd(c, sub, kTileMax, ar);
+          trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    c.join();
+    {  // f4: C <- C tril(D)^{-T}
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        split(c, c.s, p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+               0.0);
+      }
+    }
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      if (m > 0)
+        c.launch("copy_f64", 0.0, 16.0 * m * w,
+                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+      // the finished block column of L joins the split operand
+      split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
+            w, j, j, T);
+    }
+  }
+}
+
+// chol_blocked_fwd (Sec. 4.2), products in split BF16: L is split once into
+// `big`, the finished columns of L_dot into `big2`.
+void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  precompute_dinv(c, P, nb, false, ar);
+  for (auto &p : P)
+    split(c, c.s, p.L, p.ldl, p.n, p.n, 1, 0, p.mx.big, p.mx.ldb, p.n, 0, 0, p.n, (int)p.mx.ldb, 0, 0, p.mx.T);
+  const int T = P.empty() ? 2 : P[0].mx.T;
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();
+    for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T
+      MixedBatch mb(c, T, false, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *Cd = p.X + (long long)k * p.ldx + j;
+        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
+        mb.add(mop(a, p.mx.ldb, p.n, T, 0, k), mop(b, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldx, Cd, p.ldx, -1.0,
+               1.0);
+      }
+    }
+    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
+      MixedBatch mb(c, T, true);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        double *Dd = p.X + (long long)j * p.ldx + j;
+        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
+        mb.add(mop(a, p.mx.ldb, p.n, T, 0, j), mop(b, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldx, Dd, p.ldx, -1.0,
+               1.0);
+      }
+    }
+    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
+      TileBatch tb(c, T_SENS);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        const double *D = p.L + (long long)j * p.ldl + j;
+        double *Dd = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_sens(c, sub, kTileMax, ar);
+          ar.off = mark;
+        }
+      }
+    }
+    c.join();
+    {  // g4a: C_dot <- C_dot - C D_dot^T
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        double *Cd = p.X + (long long)k * p.ldx + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, j, k), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, Cd, p.ldx, Cd, p.ldx,
+               -1.0, 1.0);
+      }
+    }
+    {  // g4b: C_dot <- C_dot D^{-T}
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        split(c, c.s, p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+               0.0);
+      }
+    }
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      if (m > 0)
+        c.launch("copy_f64", 0.0, 16.0 * m * w,
+                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+      split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
+            w, j, j, T);
+    }
+  }
+}
+
 enum Op { OP_FWD, OP_REV, OP_SENS };
 
 size_t need_bytes(const int *n, int batch, int nb) {
@@ -692,7 +1149,10 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   }
   if (nmax == 0) return CD_OK;
   const int nb = pick_nb(nmax, &opt);
-  int rc = ensure_ws(h, need_bytes(n, batch, nb));
+  size_t need = need_bytes(n, batch, nb);
+  if (opt.prec != CD_FP64)
+    for (int b = 0; b < batch; ++b) need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS);
+  int rc = ensure_ws(h, need);
   if (rc) return rc;
 
   Arena ar;
@@ -713,7 +1173,8 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     P.push_back(p);
   }
   if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
-  if (opt.prec != CD_FP64 && !mixed_available()) return CD_EINVAL;
+  const bool mixed = opt.prec != CD_FP64;
+  if (mixed && (!mixed_available() || !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS, ar))) return CD_ENOMEM;
   // The step loops issue the diagonal chain on the high-priority stream (its
   // CTAs are scheduled first when SM slots free up) and the independent bulk
   // GEMM of each step on the side stream; both start after, and the caller's
@@ -724,9 +1185,9 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     c.s = h->crit;
   }
   switch (op) {
-    case OP_FWD: run_fwd(c, P, nb, ar); break;
-    case OP_REV: run_rev(c, P, nb, ar); break;
-    case OP_SENS: run_sens(c, P, nb, ar); break;
+    case OP_FWD: mixed ? run_fwd_mixed(c, P, nb, ar) : run_fwd(c, P, nb, ar); break;
+    case OP_REV: mixed ? run_rev_mixed(c, P, nb, ar) : run_rev(c, P, nb, ar); break;
+    case OP_SENS: mixed ? run_sens_mixed(c, P, nb, ar) : run_sens(c, P, nb, ar); break;
   }
   if (h->crit) {
     c.join();
@@ -817,10 +1278,11 @@ int cd_create(cd_handle **h, int device) {
   }
   x->num_sms = prop.multiProcessorCount;
   x->smem_optin = prop.sharedMemPerBlockOptin;
-  if (tile_kernels_init() != cudaSuccess || mixed_init() != CD_OK) {
+  if (tile_kernels_init() != cudaSuccess) {
     free(x);
     return CD_ECUDA;
   }
+  mixed_init();  // on failure only the CD_MIXED_* paths are unavailable
   g_init_done = true;
   if (cudaMalloc(&x->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(x->dev_err, 0, sizeof(int)) != cudaSuccess) {
     free(x);
@@ -862,7 +1324,8 @@ int cd_destroy(cd_handle *h) {
 int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes) {
   if (!h || !bytes || n_max < 0) return CD_EINVAL;
   const int nb = pick_nb(n_max, opt);
-  *bytes = need_bytes(&n_max, 1, nb) + mixed_workspace_bytes(n_max, nb, opt ? opt->prec : CD_FP64);
+  *bytes = need_bytes(&n_max, 1, nb) +
+           ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0);
   return CD_OK;
 }
 
@@ -909,6 +1372,40 @@ int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *con
 int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L, const long long *ldl,
                              double *const *Adot, const long long *lda, const cd_options *opt, void *stream) {
   return run(h, OP_SENS, batch, n, L, ldl, Adot, lda, opt, stream, nullptr);
+}
+
+int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
+                        long long ldb, double *C, long long ldc, int prec, int lower, void *stream) {
+  if (!h || M < 0 || N < 0 || K < 1 || (prec != CD_MIXED_BF16X3 && prec != CD_MIXED_BF16X6) || (lower && M != N))
+    return CD_EINVAL;
+  if (M == 0 || N == 0) return CD_OK;
+  if (!A || !B || !C || lda < K || ldb < K || ldc < N) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  if (!mixed_available()) return CD_EINVAL;
+  const int T = mix_terms(prec);
+  const long long kp = (K + 63) / 64 * 64;
+  const size_t bytes = kPartBytes + 2 * (size_t)T * ((size_t)M * kp + (size_t)N * kp) + 4 * kAlign;
+  int rc = ensure_ws(h, bytes);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar;
+  ar.base = (char *)h->ws;
+  ar.cap = h->ws_bytes;
+  cd_options opt;
+  cd_options_default(&opt);
+  Ctx c{h, s, &opt, nullptr, 0, h->gemm_slots};
+  c.part = (double *)ar.take(kPartBytes);
+  c.part_cap = kPartBytes / sizeof(double);
+  void *As = ar.take(2 * (size_t)T * M * kp);
+  void *Bs = ar.take(2 * (size_t)T * N * kp);
+  if (!As || !Bs) return CD_ENOMEM;
+  split(c, s, A, lda, M, K, 0, 0, As, kp, M, 0, 0, M, (int)kp, 0, 0, T);
+  split(c, s, B, ldb, N, K, 0, 0, Bs, kp, N, 0, 0, N, (int)kp, 0, 0, T);
+  {
+    MixedBatch mb(c, T, lower != 0);
+    mb.add(mop(As, kp, M, T, 0, 0), mop(Bs, kp, N, T, 0, 0), M, N, K, nullptr, 0, C, ldc, 1.0, 0.0);
+  }
+  return c.err;
 }
 
 int cd_get_last_device_error(cd_handle *h, int *code) {

@@ -1,9 +1,524 @@
-// Mixed-precision engine (split-BF16 operands on tcgen05 tensor cores).
+// Mixed-precision engine of libcholdiff: split-BF16 products on the sm_103a
+// tensor cores (tcgen05.mma, accumulator in tensor memory), operands staged by
+// TMA (cp.async.bulk.tensor) through a multi-stage mbarrier pipeline.
+//
+// Used for the large off-diagonal products of the blocked algorithms
+// (Sec. 4.2: the panel solves as products with the FP64 inverse of the
+// diagonal block, and the GEMM / SYRK trailing updates); the diagonal-tile
+// work stays in FP64 (cd_f64_kernels.cu).
+//
+// One CTA computes a 128 x 128 output tile over its K range:
+//   warp 0, lane 0   issues the TMA loads of all terms of A and B per 64-wide K block;
+//   warp 1, lane 0   issues tcgen05.mma for every term product of the block;
+//   warps 0-3        drain the FP32 accumulator from tensor memory (tcgen05.ld),
+//                    stage it in shared memory as FP64, and write
+//                    beta * Cin + alpha * acc (or a split-K partial) with
+//                    coalesced FP64 stores.
+// Every wait on an mbarrier gives up after 2 s of %globaltimer, sets the
+// caller's device error word to CD_ETIMEOUT and lets the CTA finish.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
 #include "cd_internal.h"
 #include "cd_mixed.h"
 
 namespace cd {
-int mixed_init() { return CD_OK; }
-bool mixed_available() { return false; }
-size_t mixed_workspace_bytes(int, int, int) { return 0; }
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int kThreads = 128;
+constexpr uint32_t kTileBytes = BM * BK * 2;  // one term of one operand per K block (BM == BN)
+constexpr unsigned long long kTimeoutNs = 2000000000ULL;
+constexpr int kMaxM = 10;
+
+struct MDesc {  // 64-byte aligned through CUtensorMap
+  CUtensorMap ta, tb;
+  const double *Cin;
+  double *Cout, *part;
+  long long ldcin, ldcout;
+  double alpha, beta;
+  int M, N, K, splits, kchunk;
+  int tiles_m, tiles_n, tile_begin;
+  int ax, ay, bx, by;
+};
+
+struct MGroup {
+  int count, total_tiles, lower, pad_;
+  int *err;
+  MDesc d[kMaxM];
+};
+static_assert(sizeof(MGroup) <= 4096, "kernel parameter block too large");
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within kTimeoutNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > kTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout: 8-row groups 1024 B apart (SBO), descriptor version 1, layout 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+          "r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int T>
+struct Terms;
+// Term products kept, smallest first: T = 2 keeps t1 t0, t0 t1, t0 t0.
+template <>
+struct Terms<2> {
+  static constexpr int n = 3;
+  __device__ static int a(int q) { return q == 0 ? 1 : 0; }
+  __device__ static int b(int q) { return q == 1 ? 1 : 0; }
+};
+// T = 3 keeps t1 t1, t2 t0, t0 t2, t1 t0, t0 t1, t0 t0.
+template <>
+struct Terms<3> {
+  static constexpr int n = 6;
+  __device__ static int a(int q) {
+    const int v[6] = {1, 2, 0, 1, 0, 0};
+    return v[q];
+  }
+  __device__ static int b(int q) {
+    const int v[6] = {1, 0, 2, 0, 1, 0};
+    return v[q];
+  }
+};
+
+template <int T>
+__host__ __device__ constexpr int stages() {
+  return T == 2 ? 3 : 2;
+}
+template <int T>
+__host__ __device__ constexpr uint32_t stage_bytes() {
+  return 2u * T * kTileBytes;
+}
+template <int T>
+constexpr size_t dyn_smem() {
+  return (size_t)stages<T>() * stage_bytes<T>() + 1024;
+}
+static_assert((size_t)BM * (BN + 1) * sizeof(double) <= (size_t)stages<2>() * stage_bytes<2>(), "staging");
+static_assert((size_t)BM * (BN + 1) * sizeof(double) <= (size_t)stages<3>() * stage_bytes<3>(), "staging");
+
+template <int T, bool LOWER>
+__global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ MGroup g) {
+  constexpr int S = stages<T>();
+  constexpr uint32_t SB = stage_bytes<T>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_err;
+
+  const int bid = blockIdx.x;
+  int p = 0;
+  while (p + 1 < g.count && bid >= g.d[p + 1].tile_begin) ++p;
+  const MDesc &d = g.d[p];
+  const int local = bid - d.tile_begin;
+  const int per_split = LOWER ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
+  const int z = local / per_split;
+  const int rem = local - z * per_split;
+  int m0, n0;
+  if (LOWER) {
+    int ti = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
+    while (ti * (ti + 1) / 2 > rem) --ti;
+    m0 = ti * BM;
+    n0 = (rem - ti * (ti + 1) / 2) * BN;
+  } else {
+    m0 = (rem / d.tiles_n) * BM;
+    n0 = (rem % d.tiles_n) * BN;
+  }
+  const int kbeg = z * d.kchunk;
+  const int kend = min(d.K, kbeg + d.kchunk);
+  const int nkb = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer: all terms of A and B for one 64-wide K block per stage.
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (kb >= S && !mbar_wait(&empty_bar[s], (uint32_t)((kb / S) - 1) & 1u)) {
+        s_err = 1;
+        break;
+      }
+      uint8_t *sa = smem + s * SB;
+      uint8_t *sb = sa + T * kTileBytes;
+      mbar_expect_tx(&full_bar[s], SB);
+      const int kx = kbeg + kb * BK;
+      tma_load_3d(sa, &d.ta, d.ax + kx, d.ay + m0, 0, &full_bar[s]);
+      tma_load_3d(sb, &d.tb, d.bx + kx, d.by + n0, 0, &full_bar[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: every kept term product of every 16-wide K step.
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (!mbar_wait(&full_bar[s], (uint32_t)(kb / S) & 1u)) {
+        s_err = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + s * SB);
+      const uint32_t sb = sa + T * kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int q = 0; q < Terms<T>::n; ++q) {
+          const uint64_t ad = sw128_desc(sa + Terms<T>::a(q) * kTileBytes + kk * 32);
+          const uint64_t bd = sw128_desc(sb + Terms<T>::b(q) * kTileBytes + kk * 32);
+          mma_bf16(tmem, ad, bd, issued ? 1u : 0u);
+          issued = 1;
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+
+  // Epilogue: accumulator (FP32, tensor memory) -> FP64 staging -> global.
+  if (!mbar_wait(&done_bar, 0)) s_err = 1;
+  tc_fence_after();
+  __syncthreads();
+  const bool err = s_err != 0;
+  double *stage = (double *)smem;
+  constexpr int LDS = BN + 1;
+  if (!err) {
+    const int row = warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) stage[row * LDS + c0 + i] = nkb > 0 ? (double)__uint_as_float(r[i]) : 0.0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+  if (err) {
+    if (threadIdx.x == 0 && g.err) atomicExch(g.err, CD_ETIMEOUT);
+    return;
+  }
+  const int j = n0 + threadIdx.x;
+  const double alpha = d.alpha, beta = d.beta;
+  for (int r = 0; r < BM; ++r) {
+    const int i = m0 + r;
+    if (i >= d.M) break;
+    if (j >= d.N || (LOWER && j > i)) continue;
+    double v = alpha * stage[r * LDS + threadIdx.x];
+    if (d.splits == 1) {
+      if (beta != 0.0) v = fma(beta, d.Cin[(long long)i * d.ldcin + j], v);
+      d.Cout[(long long)i * d.ldcout + j] = v;
+    } else {
+      d.part[((long long)z * d.M + i) * d.N + j] = v;
+    }
+  }
+}
+
+// Split-K reduction in FP64, partials summed in order.
+template <bool LOWER>
+__global__ void k_mreduce(const __grid_constant__ MGroup g) {
+  const MDesc &d = g.d[blockIdx.y];
+  if (d.splits <= 1) return;
+  const long long total = (long long)d.M * d.N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d.N), j = (int)(e - (long long)i * d.N);
+    if (LOWER && j > i) continue;
+    double s = 0.0;
+    for (int z = 0; z < d.splits; ++z) s += d.part[(long long)z * total + e];
+    if (d.beta != 0.0) s = fma(d.beta, d.Cin[(long long)i * d.ldcin + j], s);
+    d.Cout[(long long)i * d.ldcout + j] = s;
+  }
+}
+
+// FP64 -> T BF16 terms, each rounded from the exact remainder of the previous ones.
+__global__ void k_split(const SplitArgs a) {
+  __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
+  const long long tstride = a.dst_rows * a.ldd;
+  const long long total = (long long)a.dst_h * a.dst_w;
+  const int vr_n = a.transpose ? a.cols : a.rows;  // view extent in destination coordinates
+  const int vc_n = a.transpose ? a.rows : a.cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
+    const int vr = a.reg_r0 + rr - a.dst_r0, vc = a.reg_c0 + cc - a.dst_c0;
+    double x = 0.0;
+    if (vr >= 0 && vc >= 0 && vr < vr_n && vc < vc_n) {
+      const int r = a.transpose ? vc : vr, c = a.transpose ? vr : vc;
+      if (a.mode == 0) {
+        x = a.src[(long long)r * a.lds + c];
+      } else if (a.mode == 1) {
+        x = r >= c ? a.src[(long long)r * a.lds + c] : 0.0;
+      } else {
+        x = r > c ? a.src[(long long)r * a.lds + c]
+                  : (r < c ? a.src[(long long)c * a.lds + r] : 2.0 * a.src[(long long)r * a.lds + r]);
+      }
+    }
+    const long long o = (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc;
+    const __nv_bfloat16 t0 = __float2bfloat16_rn((float)x);
+    const double r1 = x - (double)__bfloat162float(t0);
+    const __nv_bfloat16 t1 = __float2bfloat16_rn((float)r1);
+    dst[o] = t0;
+    dst[tstride + o] = t1;
+    if (a.T == 3) {
+      const double r2 = r1 - (double)__bfloat162float(t1);
+      dst[2 * tstride + o] = __float2bfloat16_rn((float)r2);
+    }
+  }
+}
+
+// cuTensorMapEncodeTiled is a driver entry point; it is looked up through the
+// runtime (no link-time dependency on the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
+bool encode_map(CUtensorMap *m, const MOp &op) {
+  if (!g_encode) return false;
+  if (!op.base || (op.ld % 64) != 0 || ((uintptr_t)op.base % 16) != 0 || op.rows <= 0 || op.T < 2 || op.T > 3)
+    return false;
+  cuuint64_t dims[3] = {(cuuint64_t)op.ld, (cuuint64_t)op.rows, (cuuint64_t)op.T};
+  cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)op.ld * 2 * (cuuint64_t)op.rows};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BM, (cuuint32_t)op.T};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(op.base), dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int T, bool LOWER>
+cudaError_t launch_one(const MGroup &g, cudaStream_t s) {
+  k_mgemm<T, LOWER><<<g.total_tiles, kThreads, dyn_smem<T>(), s>>>(g);
+  return cudaGetLastError();
+}
+
+bool g_ready = false;
+
+}  // namespace
+
+int mixed_init() {
+  if (g_ready) return CD_OK;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return CD_ECUDA;
+  }
+  g_encode = (EncodeTiledFn)fn;
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_mgemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<2>());
+  if (!e) e = cudaFuncSetAttribute(k_mgemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<2>());
+  if (!e) e = cudaFuncSetAttribute(k_mgemm<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<3>());
+  if (!e) e = cudaFuncSetAttribute(k_mgemm<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<3>());
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CD_ECUDA;
+  }
+  g_ready = true;
+  return CD_OK;
+}
+
+bool mixed_available() { return g_ready; }
+
+int mixed_ctas_per_sm() { return 1; }
+
+size_t mixed_workspace_bytes(int n, int nb, int prec) {
+  if (prec == CD_FP64 || n <= 0) return 0;
+  const int T = prec == CD_MIXED_BF16X6 ? 3 : 2;
+  const size_t nbp = (size_t)((std::max(nb, 64) + 63) / 64 * 64);
+  const size_t ldb = (size_t)((n + 8 + 63) / 64 * 64), ldn = (size_t)((n + 63) / 64 * 64 + 64);
+  const size_t e = 2 * (size_t)n * ldb + (size_t)n * nbp + 2 * nbp * ldn + nbp * nbp;
+  return 2 * T * e + 16 * 256;
+}
+
+cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
+                              int *launches) {
+  if (T != 2 && T != 3) return cudaErrorInvalidValue;
+  int i = 0;
+  while (i < count) {
+    MGroup g;
+    memset(&g, 0, sizeof(g));
+    g.lower = lower ? 1 : 0;
+    g.err = dev_err;
+    bool any_split = false;
+    long long biggest = 0;
+    for (; i < count && g.count < kMaxM; ++i) {
+      const MProblem &P = probs[i];
+      if (P.M <= 0 || P.N <= 0 || P.K <= 0) continue;
+      if ((P.A.x0 % 8) || (P.B.x0 % 8) || P.A.x0 < 0 || P.B.x0 < 0 || P.A.y0 < 0 || P.B.y0 < 0 ||
+          (P.kchunk % BK) || P.kchunk <= 0 || P.A.T != T || P.B.T != T || (lower && P.M != P.N))
+        return cudaErrorInvalidValue;
+      MDesc &d = g.d[g.count];
+      if (!encode_map(&d.ta, P.A) || !encode_map(&d.tb, P.B)) return cudaErrorInvalidValue;
+      d.Cin = P.Cin;
+      d.Cout = P.Cout;
+      d.part = P.part;
+      d.ldcin = P.ldcin;
+      d.ldcout = P.ldcout;
+      d.alpha = P.alpha;
+      d.beta = P.beta;
+      d.M = P.M;
+      d.N = P.N;
+      d.K = P.K;
+      d.splits = P.splits;
+      d.kchunk = P.kchunk;
+      d.tiles_m = (P.M + BM - 1) / BM;
+      d.tiles_n = (P.N + BN - 1) / BN;
+      d.tile_begin = g.total_tiles;
+      d.ax = P.A.x0;
+      d.ay = P.A.y0;
+      d.bx = P.B.x0;
+      d.by = P.B.y0;
+      const int per = lower ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
+      g.total_tiles += per * P.splits;
+      if (P.splits > 1) {
+        any_split = true;
+        biggest = std::max(biggest, (long long)P.M * P.N);
+      }
+      ++g.count;
+    }
+    if (g.count == 0) continue;
+    cudaError_t e;
+    if (T == 2)
+      e = lower ? launch_one<2, true>(g, s) : launch_one<2, false>(g, s);
+    else
+      e = lower ? launch_one<3, true>(g, s) : launch_one<3, false>(g, s);
+    if (launches) ++*launches;
+    if (e != cudaSuccess) return e;
+    if (any_split) {
+      long long blocks = std::min<long long>(1024, (biggest + 255) / 256);
+      dim3 grid((unsigned)blocks, (unsigned)g.count);
+      if (lower)
+        k_mreduce<true><<<grid, 256, 0, s>>>(g);
+      else
+        k_mreduce<false><<<grid, 256, 0, s>>>(g);
+      if (launches) ++*launches;
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mixed_split_launch(const SplitArgs &a, cudaStream_t s) {
+  const long long total = (long long)a.dst_h * a.dst_w;
+  if (total <= 0) return cudaSuccess;
+  if (a.T < 2 || a.T > 3 || !a.dst) return cudaErrorInvalidValue;
+  long long blocks = std::min<long long>(8192, (total + 255) / 256);
+  k_split<<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace cd

@@ -1,9 +1,72 @@
 // Mixed-precision (split-BF16, tcgen05) engine interface.
+//
+// FP64 operands are split into T = 2 or 3 BF16 terms, x ~ t0 + t1 (+ t2), each
+// term rounded to nearest from the exact FP64 remainder of the previous ones.
+// A product is formed as the sum of the term products whose order is at most
+// 2^-8 (T = 2: t0 t0, t0 t1, t1 t0) or 2^-16 (T = 3: adds t0 t2, t2 t0, t1 t1)
+// relative to the leading one, accumulated in FP32 in tensor memory, and added
+// to the FP64 output in FP64.
 #pragma once
+#include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 namespace cd {
-int mixed_init();                                          // CD_OK or a CD_* error
-bool mixed_available();                                    // engine built and usable
-size_t mixed_workspace_bytes(int n, int nb, int prec);     // extra workspace for mixed calls
+
+// A K-major BF16 term array: term t, row r, column c at
+// base + (t * rows + r) * ld + c (elements).  A GEMM operand is the view with
+// origin (y0 = row, x0 = column) of such an array; rows index M (or N), columns
+// index K.  ld must be a multiple of 64 and x0 a multiple of 8.
+struct MOp {
+  const void *base;
+  long long ld;    // elements per row (multiple of 64)
+  long long rows;  // rows per term
+  int T;           // terms (2 or 3)
+  int x0, y0;      // view origin
+};
+
+// Cout = beta * Cin + alpha * op(A) op(B)^T over the views (M x K) and (N x K).
+struct MProblem {
+  MOp A, B;
+  int M, N, K;
+  const double *Cin;
+  long long ldcin;
+  double *Cout;
+  long long ldcout;
+  double alpha, beta;
+  double *part;  // split-K partials (splits * M * N doubles) when splits > 1
+  int splits;    // 1 = write Cout directly
+  int kchunk;    // K range of one split, multiple of 64
+};
+
+int mixed_init();                                       // CD_OK or a CD_* error
+bool mixed_available();                                 // engine built and usable
+size_t mixed_workspace_bytes(int n, int nb, int prec);  // extra workspace for one problem
+int mixed_ctas_per_sm();                                // resident GEMM CTAs per SM
+
+// Launch one grouped tensor-core GEMM (and its split-K reduction) over
+// `count` independent problems of the same term count and output mode.
+// dev_err: device word set to CD_ETIMEOUT if a bounded wait runs out.
+cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
+                              int *launches);
+
+// Split an FP64 view into T BF16 term arrays (see MOp).  The view is
+// rows x cols of src (lower-triangle mode 1 keeps r >= c; mode 2 is the
+// symmetric view of a lower-stored matrix with doubled diagonal); with
+// transpose the destination holds the view's transpose.  The region
+// rows [reg_r0, reg_r0 + dst_h) x cols [reg_c0, reg_c0 + dst_w) of every term
+// of dst is written; the view's (0, 0) lands at (dst_r0, dst_c0) and region
+// elements outside the view are set to zero.
+struct SplitArgs {
+  const double *src;
+  long long lds;
+  int rows, cols, mode, transpose;
+  void *dst;
+  long long ldd, dst_rows;  // term stride = dst_rows * ldd
+  int reg_r0, reg_c0, dst_h, dst_w;
+  int dst_r0, dst_c0;
+  int T;
+};
+cudaError_t mixed_split_launch(const SplitArgs &a, cudaStream_t s);
+
 }  // namespace cd

@@ -80,6 +80,7 @@ def lib():
         L.cd_profile_enable.argtypes = [_vp, _i]
         L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
         L.cd_chol_rev_noalloc.argtypes = [_i, _vp, _ll, _vp, _ll, _i, _i, _vp]
+        L.cd_mixed_gemm_debug.argtypes = [_vp, _i, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _i, _i, _vp]
         _lib = L
     return _lib
 
@@ -90,7 +91,7 @@ def exported_symbols():
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
-            "cd_chol_rev_noalloc"]
+            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug"]
 
 
 def handle(device=None):
@@ -231,6 +232,21 @@ def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64"):
     _check(lib().cd_chol_fwd_sens_batched(handle(dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_fwd_sens_batched")
     return Adots
+
+
+def mixed_gemm_debug(A, B, C, prec="bf16x3", lower=False):
+    """C = A B^T through the split-BF16 tensor-core product of the mixed path."""
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        if not t.is_cuda or t.dtype != torch.float64 or t.dim() != 2 or t.stride(1) != 1:
+            raise TypeError(f"{nm} must be a row-major CUDA float64 matrix")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    _check(lib().cd_mixed_gemm_debug(handle(A.device), M, N, K, _vp(A.data_ptr()), A.stride(0), _vp(B.data_ptr()),
+                                     B.stride(0), _vp(C.data_ptr()), C.stride(0), PREC[prec], 1 if lower else 0,
+                                     _stream(A.device)), "cd_mixed_gemm_debug")
+    return C
 
 
 def launch_count(device=None):
