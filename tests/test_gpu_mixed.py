@@ -101,5 +101,10 @@ def test_mixed_batched_ragged(cd):
     for i, c in enumerate(cases):
         if c is None:
             continue
+        a1 = torch.tensor(np.tril(c[0]), device=DEV)
+        cd.chol_fwd(a1, nb=64, prec="bf16x6")
+        r1 = torch.tensor(c[2], device=DEV)
+        cd.chol_rev(Ls[i], r1, nb=64, prec="bf16x6")
+        assert torch.equal(As[i], a1) and torch.equal(Abs[i], r1)   # batched == alone, bitwise
         assert oracle.rel_fro(As[i].cpu().numpy(), c[1]) <= OPS_TOL["bf16x6"]
         assert oracle.rel_fro(Abs[i].cpu().numpy(), oracle.chol_unblocked_rev(c[1], c[2])) <= OPS_TOL["bf16x6"]
