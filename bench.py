@@ -72,6 +72,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the served Poisson stream")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-lanes", type=int, default=2)
+    ap.add_argument("--serve-sustained-rate", type=float, default=250.0,
+                    help="a second, sustainable arrival rate (about 80%% of measured capacity)")
     return ap.parse_args()
 
 
@@ -402,6 +408,12 @@ def run_ours(args):
                                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"}
             mixed[prec] = entry
 
+    serving = None
+    if not args.no_serving:
+        del A, Ab, Ad, S0, Lb0, Sd0
+        torch.cuda.empty_cache()
+        serving = serve_bench(args, dev)
+
     cpu = None
     if d.rank == 0 and d.ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_n)
@@ -412,7 +424,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: SE covariance (ell 0.3, points U[0,1]^3, jitter 1e-4), L_bar and Sigma_dot iid N(0,1)",
         "config": ours_config(args), "ops": ops, "roofline": roofline, "kernels": kernels,
-        "mixed": mixed,
+        "mixed": mixed, "serving": serving,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
         "step_tflops": d.ws * (flops_fwd(n) + flops_sens(n) + flops_rev(n)) / (total_ms / args.steps * 1e-3) / 1e12,
     }
@@ -420,6 +432,63 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     d.close()
     return 0
+
+
+def serve_bench(args, dev):
+    """Served fwd+rev: Poisson arrivals, N log-uniform in [32, 4096], half FP64
+    and half split-BF16 (x6), 40 GB HBM budget; p50/p99 latency and solves/s,
+    next to a sample of the same requests run alone on the idle GPU."""
+    import torch
+    from paper_1602_07527_gb300 import serving as sv
+    from paper_1602_07527_gb300 import workloads as W
+    stream = W.serving_stream(seed=5, rate=args.serve_rate, duration=args.serve_seconds)
+    reqs = sv.requests_from_stream(stream, mixed_prec="bf16x6")
+    # warm the lanes (workspace growth, first-launch costs) on a few requests
+    warm = sv.Server(dev, mem_cap=40e9, lanes_per_prec=args.serve_lanes, precisions=("fp64", "bf16x6"))
+    warm.run(sv.requests_from_stream(W.serving_stream(seed=6, rate=2000.0, duration=0.01)), realtime=False)
+    torch.cuda.synchronize()
+    server = warm
+    t0 = time.perf_counter()
+    done = server.run(reqs, realtime=True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    offered = sv.summarize(done, wall)
+    by_prec = {p: sv.summarize([r for r in done if r.prec == p], wall) for p in ("fp64", "bf16x6")}
+    # the same kinds of requests alone: a sample of 40, one at a time on the idle GPU
+    rng = np.random.default_rng(7)
+    sample = [reqs[i] for i in sorted(rng.choice(len(reqs), size=min(40, len(reqs)), replace=False))]
+    alone = []
+    for r in sample:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sv.solve_alone(r, dev)
+        torch.cuda.synchronize()
+        alone.append(time.perf_counter() - t)
+    served_sample = [r.t_done - r.t_admit for r in done if r.rid in {q.rid for q in sample}]
+    # the same mix at a rate the GPU sustains: queueing no longer dominates
+    sus_stream = W.serving_stream(seed=8, rate=args.serve_sustained_rate, duration=2.0)
+    sus_reqs = sv.requests_from_stream(sus_stream, mixed_prec="bf16x6")
+    t1 = time.perf_counter()
+    sus_done = server.run(sus_reqs, realtime=True)
+    torch.cuda.synchronize()
+    sus_wall = time.perf_counter() - t1
+    sustained = sv.summarize(sus_done, sus_wall)
+    sustained["rate"] = args.serve_sustained_rate
+    sustained["by_precision"] = {p: sv.summarize([r for r in sus_done if r.prec == p], sus_wall)
+                                 for p in ("fp64", "bf16x6")}
+    server.close()
+    mean_n3 = float(np.mean([r.n ** 3 for r in reqs]))
+    return {"stream": (f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, N log-uniform [32, 4096], "
+                       f"50/50 FP64 / split-BF16 x6, SE ell 0.3 on [0,1]^3 + {sv.SE_JITTER:g} I, 40 GB budget, "
+                       f"{args.serve_lanes} lanes per precision"),
+            "offered_tflops": args.serve_rate * mean_n3 / 1e12,
+            "served": offered, "served_by_precision": by_prec, "sustained": sustained,
+            "peak_bytes": server.peak_bytes,
+            "host_launch_s": server.host_launch_s, "host_phase_s": server.host_phase_s,
+            "alone_sample": {"requests": len(alone), "p50_ms": 1e3 * sv.percentile(alone, 50),
+                             "p99_ms": 1e3 * sv.percentile(alone, 99),
+                             "solves_per_s": len(alone) / sum(alone),
+                             "served_service_p50_ms_same_requests": 1e3 * sv.percentile(served_sample, 50)}}
 
 
 def main():

@@ -57,8 +57,8 @@
  *   n == 0 is a valid no-op.
  *
  * Ownership.  The caller owns every matrix, info array and stream.  The
- *   handle owns its workspace (grown on demand with cudaMalloc, released by
- *   cd_destroy) and must not be used by two host threads at once; calls that
+ *   handle owns its workspace (grown on demand in stream order with
+ *   cudaMallocAsync on the call's stream, released by cd_destroy) and must not be used by two host threads at once; calls that
  *   share a handle must be ordered on one stream (they share its workspace).
  */
 #ifndef LIBCHOLDIFF_H
@@ -115,7 +115,7 @@ void cd_options_default(cd_options *opt);
  * allocating. */
 int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes);
 
-/* Grow the handle's workspace to at least `bytes` now (synchronous cudaMalloc). */
+/* Grow the handle's workspace to at least `bytes` now (returns when it is allocated). */
 int cd_reserve(cd_handle *h, size_t bytes);
 
 /*
@@ -212,6 +212,17 @@ int cd_chol_rev_noalloc(int n, const double *L, long long ldl, double *Abar, lon
  */
 int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
                         long long ldb, double *C, long long ldc, int prec, int lower, void *stream);
+
+/*
+ * Scheduling knob (no counterpart in the paper).  Every call runs its
+ * diagonal chain on one internal stream and the step's independent bulk
+ * product on another, both forked from and joined back into the caller's
+ * stream.  This sets their CUDA stream priorities (clamped to the device's
+ * range; lower numbers are higher priority; defaults: greatest for the
+ * chain, least for the bulk).  Handles serving latency-critical work can be
+ * raised above others that share the GPU.  Synchronises the handle's device.
+ */
+int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority);
 
 /* Read and clear the handle's device error word (synchronises the handle's
  * device).  *code receives CD_OK or a negative CD_* code. */

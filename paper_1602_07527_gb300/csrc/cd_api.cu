@@ -330,6 +330,28 @@ struct TileBatch {
   ~TileBatch() { flush(); }
 };
 
+// Accumulates the panel copies of all problems of one step into one launch.
+struct CopyBatch {
+  Ctx &c;
+  CopyGroup g;
+  double bytes = 0;
+  explicit CopyBatch(Ctx &ctx) : c(ctx) { memset(&g, 0, sizeof(g)); }
+  void add(const double *src, long long lds, double *dst, long long ldd, int rows, int cols) {
+    if (rows <= 0 || cols <= 0) return;
+    if (g.count == kMaxCopy) flush();
+    CopyDesc &d = g.d[g.count++];
+    d.src = src; d.dst = dst; d.lds = lds; d.ldd = ldd; d.rows = rows; d.cols = cols;
+    bytes += 16.0 * rows * cols;
+  }
+  void flush() {
+    if (g.count == 0) return;
+    c.launch("copy_f64", 0.0, bytes, [&] { return launch_copy_group(g, c.s); });
+    g.count = 0;
+    bytes = 0;
+  }
+  ~CopyBatch() { flush(); }
+};
+
 TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double *inv, long long ldinv, int t,
                int *info = nullptr, int col0 = 0) {
   TileDesc d;
@@ -471,13 +493,14 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv, nb, nullptr, 0, p.W, nb, 1.0, 0.0);
       }
     }
-    for (auto &p : P) {
-      const int j = s * nb;
-      if (j >= p.n) continue;
-      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0)
-        c.launch("copy_f64", 0.0, 16.0 * m * w,
-                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+    {
+      CopyBatch cb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+      }
     }
   }
 }
@@ -504,13 +527,14 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                nb, 1.0, 0.0);
       }
     }
-    for (auto &p : P) {
-      int j, k;
-      if (!blk(p, s, j, k)) continue;
-      const int w = k - j, m = p.n - k;
-      if (m > 0)
-        c.launch("copy_f64", 0.0, 16.0 * m * w,
-                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+    {
+      CopyBatch cb(c);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+      }
     }
     c.fork();  // r2 writes B_bar only; r3, r4, r5 neither read nor write it
     {  // r2: B_bar <- B_bar - C_bar R
@@ -650,13 +674,14 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                nb, 1.0, 0.0);
       }
     }
-    for (auto &p : P) {
-      const int j = s * nb;
-      if (j >= p.n) continue;
-      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0)
-        c.launch("copy_f64", 0.0, 16.0 * m * w,
-                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
+    {
+      CopyBatch cb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+      }
     }
   }
 }
@@ -691,6 +716,37 @@ void split(Ctx &c, cudaStream_t st, const double *src, long long lds, int rows, 
   a.T = T;
   c.launch("split_bf16", 0.0, (8.0 + 2.0 * T) * h * w, st, [&] { return mixed_split_launch(a, st); });
 }
+
+// Accumulates the operand splits of all problems of one phase into grouped launches.
+struct SplitBatch {
+  Ctx &c;
+  std::vector<SplitArgs> v;
+  double bytes = 0;
+  explicit SplitBatch(Ctx &ctx) : c(ctx) {}
+  void add(const double *src, long long lds, int rows, int cols, int mode, int transpose, void *dst, long long ldd,
+           long long dst_rows, int reg_r0, int reg_c0, int h, int w, int dst_r0, int dst_c0, int T) {
+    if (h <= 0 || w <= 0) return;
+    SplitArgs a;
+    a.src = src; a.lds = lds; a.rows = rows; a.cols = cols; a.mode = mode; a.transpose = transpose;
+    a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
+    a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
+    a.T = T;
+    v.push_back(a);
+    bytes += (8.0 + 2.0 * T) * h * w;
+  }
+  void flush() {
+    if (v.empty()) return;
+    c.launch("split_bf16", 0.0, bytes, [&] {
+      int l = 0;
+      const cudaError_t e = mixed_split_group_launch(v.data(), (int)v.size(), c.s, &l);
+      if (l > 1) c.h->launches += l - 1;
+      return e;
+    });
+    v.clear();
+    bytes = 0;
+  }
+  ~SplitBatch() { flush(); }
+};
 
 // Accumulates tensor-core products of one kind into grouped launches.
 struct MixedBatch {
@@ -823,9 +879,12 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar) {
 // (columns shifted by pad so that every block boundary is a multiple of 8).
 void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   precompute_dinv(c, P, nb, true, ar);
-  for (auto &p : P) {
-    const auto &x = p.mx;
-    split(c, c.s, p.L, p.ldl, p.n, p.n, 1, 1, x.big, x.ldb, p.n, 0, 0, p.n, (int)x.ldb, 0, x.pad, x.T);
+  {
+    SplitBatch sb(c);
+    for (auto &p : P) {
+      const auto &x = p.mx;
+      sb.add(p.L, p.ldl, p.n, p.n, 1, 1, x.big, x.ldb, p.n, 0, 0, p.n, (int)x.ldb, 0, x.pad, x.T);
+    }
   }
   const int T = P.empty() ? 2 : P[0].mx.T;
   int nmax = 0;
@@ -838,13 +897,16 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     {  // r1: W = C_bar D^{-1}; W -> C_bar; W and W^T split for r2, r3
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        if (m <= 0) continue;
-        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-        split(c, c.s, p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 1, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k)) continue;
+          const int w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 1, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+        }
       }
       MixedBatch mb(c, T, false);
       for (auto &p : P) {
@@ -855,15 +917,18 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                0.0);
       }
     }
-    for (auto &p : P) {
-      int j, k;
-      if (!blk(p, s, j, k)) continue;
-      const int w = k - j, m = p.n - k;
-      if (m <= 0) continue;
-      c.launch("copy_f64", 0.0, 16.0 * m * w,
-               [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
-      split(c, c.s, p.W, nb, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-      split(c, c.s, p.W, nb, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, (int)p.mx.ldn, 0, 0, T);
+    {
+      CopyBatch cb(c);
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+        sb.add(p.W, nb, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        sb.add(p.W, nb, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, (int)p.mx.ldn, 0, 0, T);
+      }
     }
     c.fork();
     {  // r2 (side stream): B_bar <- B_bar - C_bar R
@@ -910,12 +975,15 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // r5: R_bar <- R_bar - G L[j:n, 0:j],  G = [D_bar + D_bar^T, C_bar^T]
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k) || j == 0) continue;
-        const int w = k - j;
-        split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, w, p.n - j, 2, 0, p.mx.P3, p.mx.ldn, nb, 0, 0, w,
-              (int)p.mx.ldn, 0, 0, T);
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k) || j == 0) continue;
+          const int w = k - j;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, p.n - j, 2, 0, p.mx.P3, p.mx.ldn, nb, 0, 0, w,
+                (int)p.mx.ldn, 0, 0, T);
+        }
       }
       MixedBatch mb(c, T, false);
       for (auto &p : P) {
@@ -985,13 +1053,16 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        if (m <= 0) continue;
-        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-        split(c, c.s, p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+        }
       }
       MixedBatch mb(c, T, false);
       for (auto &p : P) {
@@ -1002,16 +1073,20 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                0.0);
       }
     }
-    for (auto &p : P) {
-      const int j = s * nb;
-      if (j >= p.n) continue;
-      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0)
-        c.launch("copy_f64", 0.0, 16.0 * m * w,
-                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
-      // the finished block column of L joins the split operand
-      split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
-            w, j, j, T);
+    {
+      CopyBatch cb(c);
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+        // the finished block column of L joins the split operand
+        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
+              w, j, j, T);
+      }
+      cb.flush();  // the solved panel must be in place before it is split
+      sb.flush();
     }
   }
 }
@@ -1020,8 +1095,11 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // `big`, the finished columns of L_dot into `big2`.
 void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   precompute_dinv(c, P, nb, false, ar);
-  for (auto &p : P)
-    split(c, c.s, p.L, p.ldl, p.n, p.n, 1, 0, p.mx.big, p.mx.ldb, p.n, 0, 0, p.n, (int)p.mx.ldb, 0, 0, p.mx.T);
+  {
+    SplitBatch sb(c);
+    for (auto &p : P)
+      sb.add(p.L, p.ldl, p.n, p.n, 1, 0, p.mx.big, p.mx.ldb, p.n, 0, 0, p.n, (int)p.mx.ldb, 0, 0, p.mx.T);
+  }
   const int T = P.empty() ? 2 : P[0].mx.T;
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
@@ -1075,12 +1153,15 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     c.join();
     {  // g4a: C_dot <- C_dot - C D_dot^T
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        if (m <= 0) continue;
-        split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+        }
       }
       MixedBatch mb(c, T, false);
       for (auto &p : P) {
@@ -1093,13 +1174,16 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // g4b: C_dot <- C_dot D^{-T}
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        if (m <= 0) continue;
-        split(c, c.s, p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-        split(c, c.s, p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+        }
       }
       MixedBatch mb(c, T, false);
       for (auto &p : P) {
@@ -1110,15 +1194,19 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                0.0);
       }
     }
-    for (auto &p : P) {
-      const int j = s * nb;
-      if (j >= p.n) continue;
-      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-      if (m > 0)
-        c.launch("copy_f64", 0.0, 16.0 * m * w,
-                 [&] { return launch_copy(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w, c.s); });
-      split(c, c.s, p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
-            w, j, j, T);
+    {
+      CopyBatch cb(c);
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
+              w, j, j, T);
+      }
+      cb.flush();  // the solved panel must be in place before it is split
+      sb.flush();
     }
   }
 }
@@ -1131,15 +1219,19 @@ size_t need_bytes(const int *n, int batch, int nb) {
   return b;
 }
 
-int ensure_ws(cd_handle *h, size_t bytes) {
+// Grow the workspace in stream order: the old buffer is released after the
+// work already enqueued on `s` (which every earlier call of this handle has
+// joined back into) and the new one is usable by work enqueued after it, so
+// growing never waits for the device.
+int ensure_ws(cd_handle *h, size_t bytes, cudaStream_t s) {
   if (bytes <= h->ws_bytes) return CD_OK;
   if (h->ws) {
-    cudaDeviceSynchronize();  // earlier calls may still use the old buffer
-    cudaFree(h->ws);
+    cudaFreeAsync(h->ws, s);
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
-  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+  bytes = bytes + bytes / 8;  // headroom: fewer regrowths for slowly growing batches
+  if (cudaMallocAsync(&h->ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     h->ws = nullptr;
     return CD_ENOMEM;
@@ -1177,7 +1269,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   size_t need = need_bytes(n, batch, nb);
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b) need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS);
-  int rc = ensure_ws(h, need);
+  int rc = ensure_ws(h, need, s);
   if (rc) return rc;
 
   Arena ar;
@@ -1357,7 +1449,9 @@ int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size
 int cd_reserve(cd_handle *h, size_t bytes) {
   if (!h) return CD_EINVAL;
   DeviceGuard guard(h->device);
-  return ensure_ws(h, bytes);
+  const int rc = ensure_ws(h, bytes, nullptr);
+  if (rc == CD_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) return CD_ECUDA;
+  return rc;
 }
 
 int cd_chol_fwd(cd_handle *h, int n, double *A, long long lda, const cd_options *opt, void *stream, int *info) {
@@ -1399,6 +1493,26 @@ int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double
   return run(h, OP_SENS, batch, n, L, ldl, Adot, lda, opt, stream, nullptr);
 }
 
+int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {
+  if (!h) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  auto clamp = [&](int p) { return std::min(lo, std::max(hi, p)); };
+  if (cudaDeviceSynchronize() != cudaSuccess) return CD_ECUDA;
+  cudaStream_t crit = nullptr, side = nullptr;
+  if (cudaStreamCreateWithPriority(&crit, cudaStreamNonBlocking, clamp(chain_priority)) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, clamp(bulk_priority)) != cudaSuccess) {
+    if (crit) cudaStreamDestroy(crit);
+    return CD_ECUDA;
+  }
+  cudaStreamDestroy(h->crit);
+  cudaStreamDestroy(h->side);
+  h->crit = crit;
+  h->side = side;
+  return CD_OK;
+}
+
 int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
                         long long ldb, double *C, long long ldc, int prec, int lower, void *stream) {
   if (!h || M < 0 || N < 0 || K < 1 || (prec != CD_MIXED_BF16X3 && prec != CD_MIXED_BF16X6) || (lower && M != N))
@@ -1410,9 +1524,9 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
   const int T = mix_terms(prec);
   const long long kp = (K + 63) / 64 * 64;
   const size_t bytes = kPartBytes + 2 * (size_t)T * ((size_t)M * kp + (size_t)N * kp) + 4 * kAlign;
-  int rc = ensure_ws(h, bytes);
-  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(h, bytes, s);
+  if (rc) return rc;
   Arena ar;
   ar.base = (char *)h->ws;
   ar.cap = h->ws_bytes;

@@ -434,6 +434,26 @@ cudaError_t launch_copy(const double *src, long long lds, double *dst, long long
   return cudaGetLastError();
 }
 
+__global__ void k_copy_group(const __grid_constant__ CopyGroup g) {
+  const CopyDesc &d = g.d[blockIdx.y];
+  const long long total = (long long)d.rows * d.cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d.cols), j = (int)(e - (long long)i * d.cols);
+    d.dst[(long long)i * d.ldd + j] = d.src[(long long)i * d.lds + j];
+  }
+}
+
+cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s) {
+  if (g.count <= 0) return cudaSuccess;
+  long long biggest = 0;
+  for (int p = 0; p < g.count; ++p) biggest = std::max(biggest, (long long)g.d[p].rows * g.d[p].cols);
+  if (biggest <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>(1024, (biggest + 255) / 256);
+  k_copy_group<<<dim3((unsigned)blocks, (unsigned)g.count), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
 // Strict upper triangle <- mirror of the strict lower one, through a 32 x 32
 // shared tile so that both the reads and the writes are coalesced.
 __global__ void k_mirror(double *A, long long lda, int n) {

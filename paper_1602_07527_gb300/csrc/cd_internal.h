@@ -61,6 +61,19 @@ struct TileGroup {
 
 enum TileOp { T_POTF2 = 0, T_REV = 1, T_SENS = 2, T_TRTRI = 3 };
 
+// Grouped 2-D copies (one launch for the panels of every problem of a step).
+struct CopyDesc {
+  const double *src;
+  double *dst;
+  long long lds, ldd;
+  int rows, cols;
+};
+constexpr int kMaxCopy = 96;
+struct CopyGroup {
+  int count, pad_;
+  CopyDesc d[kMaxCopy];
+};
+
 // ---------------------------------------------------------------------------
 // Mixed-precision (split-BF16 tcgen05) engine: see cd_mixed.cu.
 // ---------------------------------------------------------------------------
@@ -92,6 +105,7 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s);
 cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, int rows,
                         int cols, cudaStream_t s);
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
+cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
 int gemm_ctas_per_sm();  // resident CTAs of the FP64 GEMM per SM
 }  // namespace cd

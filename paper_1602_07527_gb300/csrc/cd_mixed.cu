@@ -341,14 +341,13 @@ __global__ void k_mreduce(const __grid_constant__ MGroup g) {
 }
 
 // FP64 -> T BF16 terms, each rounded from the exact remainder of the previous ones.
-__global__ void k_split(const SplitArgs a) {
+__device__ void split_body(const SplitArgs &a, long long first, long long stride) {
   __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
   const long long tstride = a.dst_rows * a.ldd;
   const long long total = (long long)a.dst_h * a.dst_w;
   const int vr_n = a.transpose ? a.cols : a.rows;  // view extent in destination coordinates
   const int vc_n = a.transpose ? a.rows : a.cols;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = first; e < total; e += stride) {
     const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
     const int vr = a.reg_r0 + rr - a.dst_r0, vc = a.reg_c0 + cc - a.dst_c0;
     double x = 0.0;
@@ -382,6 +381,21 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
+
+__global__ void k_split(const SplitArgs a) {
+  split_body(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+constexpr int kMaxSplit = 36;
+struct SplitGroup {
+  int count, pad_;
+  SplitArgs a[kMaxSplit];
+};
+static_assert(sizeof(SplitGroup) <= 4096, "kernel parameter block too large");
+
+__global__ void k_split_group(const __grid_constant__ SplitGroup g) {
+  split_body(g.a[blockIdx.y], (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
 
 bool encode_map(CUtensorMap *m, const MOp &op) {
   if (!g_encode) return false;
@@ -508,6 +522,28 @@ cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lowe
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t s, int *launches) {
+  int i = 0;
+  while (i < count) {
+    SplitGroup g;
+    memset(&g, 0, sizeof(g));
+    long long biggest = 0;
+    for (; i < count && g.count < kMaxSplit; ++i) {
+      if ((long long)a[i].dst_h * a[i].dst_w <= 0) continue;
+      if (a[i].T < 2 || a[i].T > 3 || !a[i].dst) return cudaErrorInvalidValue;
+      g.a[g.count++] = a[i];
+      biggest = std::max(biggest, (long long)a[i].dst_h * a[i].dst_w);
+    }
+    if (g.count == 0) continue;
+    const long long blocks = std::min<long long>(4096, (biggest + 255) / 256);
+    k_split_group<<<dim3((unsigned)blocks, (unsigned)g.count), 256, 0, s>>>(g);
+    if (launches) ++*launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -68,5 +68,7 @@ struct SplitArgs {
   int T;
 };
 cudaError_t mixed_split_launch(const SplitArgs &a, cudaStream_t s);
+// Several independent splits in one launch.
+cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t s, int *launches);
 
 }  // namespace cd

@@ -80,6 +80,7 @@ def lib():
         L.cd_profile_enable.argtypes = [_vp, _i]
         L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
         L.cd_chol_rev_noalloc.argtypes = [_i, _vp, _ll, _vp, _ll, _i, _i, _vp]
+        L.cd_set_priorities.argtypes = [_vp, _i, _i]
         L.cd_mixed_gemm_debug.argtypes = [_vp, _i, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _i, _i, _vp]
         _lib = L
     return _lib
@@ -91,7 +92,7 @@ def exported_symbols():
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
-            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug"]
+            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities"]
 
 
 def handle(device=None):
@@ -128,6 +129,10 @@ class Handle:
             raise CholDiffError(rc, "cd_create")
         self.ptr = hp.value
         self.device = dev
+
+    def set_priorities(self, chain, bulk):
+        """CUDA priorities of the handle's internal streams (lower = higher priority)."""
+        _check(lib().cd_set_priorities(_vp(self.ptr), int(chain), int(bulk)), "cd_set_priorities")
 
     def close(self):
         if self.ptr:

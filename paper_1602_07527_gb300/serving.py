@@ -6,22 +6,22 @@ L = cd_chol_fwd(Sigma) followed by tril(Sigma_bar) = cd_chol_rev(L, L_bar)
 (Sec. 4.2), with L kept resident on the device between the two.
 
 The loop replays the arrival times in real time.  Requests that have arrived
-wait in a FIFO queue; whenever a lane (a CUDA stream with its own library
-handle and workspace) is free and the HBM budget allows, the queue's head is
-admitted as one ragged batch: its requests run together inside the same
-grouped kernels (cd_chol_*_batched), and batches of different lanes overlap
-on the device.  A batch completes when its CUDA event does; its memory then
-returns to the budget and newly arrived requests are admitted.  Precision is
-per request (FP64 or split-BF16); requests of one precision in a batch share
-one call.
+wait in a FIFO queue per precision; whenever a lane of that precision (a CUDA
+stream with its own library handle and workspace) has room and the HBM budget
+allows, the queue's head is admitted as one ragged batch: its requests run
+together inside the same grouped kernels (cd_chol_*_batched), and the
+batches of all lanes overlap on the device.  Sub-batches complete through
+their own CUDA events; their memory then returns to the budget and newly
+arrived requests are admitted.
 """
 import collections
 import dataclasses
 import math
+import queue
+import threading
 import time
 from typing import List, Optional
 
-import numpy as np
 import torch
 
 from . import native
@@ -59,13 +59,14 @@ def request_bytes(n: int, prec: str) -> int:
 
 
 def build_inputs(req: Request, device, ell=SE_ELL, jitter=SE_JITTER):
-    """The request's payload: Sigma from its seeded points, L_bar from its seed."""
-    rng = np.random.default_rng([req.seed, 0])
-    X = torch.tensor(rng.uniform(size=(req.n, 3)), device=device)
-    S = torch.cdist(X, X).square_().mul_(-0.5 / (ell * ell)).exp_()
-    S.diagonal().add_(jitter)
+    """The request's payload, drawn on the device from the request's seed
+    (no host-to-device copy, which would block the launching thread):
+    points uniform in [0,1]^3 -> SE covariance Sigma, and L_bar iid N(0,1)."""
     g = torch.Generator(device=device)
     g.manual_seed(int(req.seed) & 0x7FFFFFFFFFFFFFFF)
+    X = torch.rand(req.n, 3, generator=g, device=device, dtype=torch.float64)
+    S = torch.cdist(X, X).square_().mul_(-0.5 / (ell * ell)).exp_()
+    S.diagonal().add_(jitter)
     Lb = torch.randn(req.n, req.n, generator=g, device=device, dtype=torch.float64).tril_()
     return S, Lb
 
@@ -79,59 +80,123 @@ def solve_alone(req: Request, device, nb=0):
 
 
 class _Lane:
-    def __init__(self, device):
-        self.stream = torch.cuda.Stream(device)
+    """One CUDA stream with its own library handle and host thread, serving
+    one precision.  The thread turns admitted batches into launches (the
+    library's host loop runs without holding the GIL), so lanes enqueue work
+    in parallel while the scheduler thread keeps admitting and completing."""
+
+    def __init__(self, device, prec, high):
+        self.device = device
+        self.prec = prec
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -5)
+        self.stream = torch.cuda.Stream(device, priority=hi if high else 0)
         self.handle = native.Handle(device)
-        self.batch: List[Request] = []
-        self.event = None
-        self.bytes = 0
+        # cheap (split-BF16) requests are scheduled ahead of FP64 ones on a shared GPU
+        self.handle.set_priorities(hi if high else min(0, hi + 2), hi + 1 if high else 0)
+        self.inflight = collections.deque()   # (event, requests, bytes, last), in stream order
+        self.lock = threading.Lock()
+        self.batches = 0                      # admitted batches not yet complete (scheduler thread only)
+        self.launch_s = 0.0
+        self.phase_s = {"inputs": 0.0, "fwd": 0.0, "rev": 0.0}
+        self.work = queue.Queue()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def _loop(self):
+        torch.cuda.set_device(self.device)
+        while True:
+            item = self.work.get()
+            if item is None:
+                return
+            server, batch = item
+            t = time.perf_counter()
+            entries = server._launch(self, batch)
+            self.launch_s += time.perf_counter() - t
+            with self.lock:
+                self.inflight.extend(entries)
+
+    def close(self):
+        self.work.put(None)
+        self.thread.join()
+        self.handle.close()
 
 
 class Server:
-    def __init__(self, device="cuda:0", mem_cap=40e9, lanes=2, max_batch=64, nb=0, keep_results=False):
+    """Continuous batching over `lanes_per_prec` lanes per precision.
+
+    A lane accepts a new batch while up to `depth` earlier batches are still
+    queued or running on its stream, so the stream never idles between
+    batches.  An admitted batch is sorted by size and launched as size-class
+    sub-batches (sizes within a factor of two), each with its own completion
+    event, so that small requests finish without waiting for large ones.
+    """
+
+    def __init__(self, device="cuda:0", mem_cap=40e9, lanes_per_prec=2, max_batch=64, nb=0, depth=2,
+                 keep_results=False, precisions=("fp64", "bf16x6", "bf16x3")):
         self.device = torch.device(device)
         self.mem_cap = float(mem_cap)
         self.max_batch = int(max_batch)
         self.nb = nb
+        self.depth = int(depth)
         self.keep = keep_results
-        self.lanes = [_Lane(self.device) for _ in range(lanes)]
+        self.lanes = [_Lane(self.device, p, p != "fp64") for p in precisions for _ in range(lanes_per_prec)]
         self.peak_bytes = 0.0
+
+    @property
+    def host_launch_s(self):
+        return sum(ln.launch_s for ln in self.lanes)
+
+    @property
+    def host_phase_s(self):
+        return {k: sum(ln.phase_s[k] for ln in self.lanes) for k in ("inputs", "fwd", "rev")}
 
     def close(self):
         for ln in self.lanes:
-            ln.handle.close()
+            ln.close()
 
     def _launch(self, lane: _Lane, batch: List[Request]):
+        """Enqueue one admitted batch on the lane (lane thread); returns its entries."""
+        out = []
+        batch = sorted(batch, key=lambda r: r.n)
+        classes = collections.OrderedDict()
+        for r in batch:
+            classes.setdefault(max(1, r.n).bit_length(), []).append(r)
         with torch.cuda.stream(lane.stream):
-            bufs = {}
-            for r in batch:
-                bufs[r.rid] = build_inputs(r, self.device)
-            for prec in ("fp64", "bf16x6", "bf16x3"):
-                grp = [r for r in batch if r.prec == prec]
-                if not grp:
-                    continue
-                As = [bufs[r.rid][0] for r in grp]
-                Abs = [bufs[r.rid][1] for r in grp]
-                info = native.chol_fwd_batched(As, nb=self.nb, prec=prec, handle_=lane.handle)
-                native.chol_rev_batched(As, Abs, nb=self.nb, prec=prec, handle_=lane.handle)
-                for i, r in enumerate(grp):
-                    if self.keep:
+            for grp in classes.values():
+                t = time.perf_counter()
+                bufs = [build_inputs(r, self.device) for r in grp]
+                As = [b[0] for b in bufs]
+                Abs = [b[1] for b in bufs]
+                t1 = time.perf_counter()
+                info = native.chol_fwd_batched(As, nb=self.nb, prec=lane.prec, handle_=lane.handle)
+                t2 = time.perf_counter()
+                native.chol_rev_batched(As, Abs, nb=self.nb, prec=lane.prec, handle_=lane.handle)
+                t3 = time.perf_counter()
+                lane.phase_s["inputs"] += t1 - t
+                lane.phase_s["fwd"] += t2 - t1
+                lane.phase_s["rev"] += t3 - t2
+                if self.keep:
+                    for i, r in enumerate(grp):
                         r.sigma_bar = Abs[i]
                         r.info = info[i:i + 1]
-            lane.event = torch.cuda.Event()
-            lane.event.record(lane.stream)
-        lane.batch = batch
-        lane.bytes = sum(request_bytes(r.n, r.prec) for r in batch)
+                ev = torch.cuda.Event()
+                ev.record(lane.stream)
+                out.append((ev, grp, sum(request_bytes(r.n, r.prec) for r in grp), False))
+        out[-1] = out[-1][:3] + (True,)
+        return out
 
     def run(self, requests: List[Request], realtime: bool = True):
         """Serve `requests` (arrival times replayed in real time unless
         realtime=False, which releases every request at t = 0).  Returns the
         list of completed requests with t_admit / t_done filled in."""
         reqs = sorted(requests, key=lambda r: r.t_arrival)
+        precs = {ln.prec for ln in self.lanes}
         for r in reqs:
             if request_bytes(r.n, r.prec) > self.mem_cap:
                 raise ValueError(f"request {r.rid} alone exceeds the memory cap")
-        pending = collections.deque()
+            if r.prec not in precs:
+                raise ValueError(f"no lane serves precision {r.prec}")
+        pending = {p: collections.deque() for p in precs}
         done: List[Request] = []
         in_use = 0.0
         i = 0
@@ -139,38 +204,42 @@ class Server:
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
             while i < len(reqs) and (not realtime or reqs[i].t_arrival <= now):
-                pending.append(reqs[i])
+                pending[reqs[i].prec].append(reqs[i])
                 i += 1
             progressed = False
-            for ln in self.lanes:
-                if ln.batch and ln.event.query():
-                    t = time.perf_counter() - t0
-                    for r in ln.batch:
-                        r.t_done = t
-                    done.extend(ln.batch)
-                    in_use -= ln.bytes
-                    ln.batch, ln.bytes = [], 0
-                    progressed = True
-            for ln in self.lanes:
-                if ln.batch or not pending:
-                    continue
-                batch, need = [], 0.0
-                while pending and len(batch) < self.max_batch:
-                    b = request_bytes(pending[0].n, pending[0].prec)
-                    if in_use + need + b > self.mem_cap:
+            for ln in self.lanes:                      # completions, in stream order
+                with ln.lock:
+                    while ln.inflight and ln.inflight[0][0].query():
+                        _, grp, b, last = ln.inflight.popleft()
+                        t = time.perf_counter() - t0
+                        for r in grp:
+                            r.t_done = t
+                        done.extend(grp)
+                        in_use -= b
+                        if last:
+                            ln.batches -= 1
+                        progressed = True
+            for ln in self.lanes:                      # admissions
+                q = pending[ln.prec]
+                while q and ln.batches < self.depth:
+                    batch, need = [], 0.0
+                    while q and len(batch) < self.max_batch:
+                        b = request_bytes(q[0].n, q[0].prec)
+                        if in_use + need + b > self.mem_cap:
+                            break
+                        r = q.popleft()
+                        r.t_admit = time.perf_counter() - t0
+                        batch.append(r)
+                        need += b
+                    if not batch:
                         break
-                    r = pending.popleft()
-                    r.t_admit = time.perf_counter() - t0
-                    batch.append(r)
-                    need += b
-                if not batch:
-                    break
-                in_use += need
-                self.peak_bytes = max(self.peak_bytes, in_use)
-                self._launch(ln, batch)
-                progressed = True
+                    in_use += need
+                    self.peak_bytes = max(self.peak_bytes, in_use)
+                    ln.batches += 1
+                    ln.work.put((self, batch))
+                    progressed = True
             if not progressed:
-                if i < len(reqs) and not pending and realtime:
+                if i < len(reqs) and realtime and not any(pending.values()):
                     time.sleep(max(0.0, min(1e-3, reqs[i].t_arrival - (time.perf_counter() - t0))))
                 else:
                     time.sleep(5e-5)

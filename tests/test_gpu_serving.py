@@ -29,7 +29,7 @@ def _stream(serving, count, n_hi, seed=5):
 def test_served_equals_alone(srv):
     reqs = _stream(srv, 48, 600)
     assert {r.prec for r in reqs} == {"fp64", "bf16x6"}
-    server = srv.Server(DEV, mem_cap=24e6, lanes=2, max_batch=8, keep_results=True)
+    server = srv.Server(DEV, mem_cap=24e6, lanes_per_prec=2, max_batch=8, keep_results=True)
     done = server.run(reqs)
     torch.cuda.synchronize()
     assert len(done) == len(reqs)
@@ -46,7 +46,7 @@ def test_served_equals_alone(srv):
 
 def test_served_matches_oracle(srv):
     reqs = [r for r in _stream(srv, 30, 300, seed=9) if r.prec == "fp64"][:6]
-    server = srv.Server(DEV, mem_cap=1e9, lanes=2, max_batch=4, keep_results=True)
+    server = srv.Server(DEV, mem_cap=1e9, lanes_per_prec=2, max_batch=4, keep_results=True)
     done = server.run(reqs, realtime=False)
     torch.cuda.synchronize()
     for r in done:
@@ -62,7 +62,7 @@ def test_served_matches_oracle(srv):
 def test_admission_with_tight_budget(srv):
     reqs = _stream(srv, 12, 400, seed=11)
     cap = max(srv.request_bytes(r.n, r.prec) for r in reqs) * 1.01
-    server = srv.Server(DEV, mem_cap=cap, lanes=2, max_batch=16)
+    server = srv.Server(DEV, mem_cap=cap, lanes_per_prec=1, max_batch=16)
     done = server.run(reqs, realtime=False)
     assert len(done) == len(reqs)
     assert server.peak_bytes <= cap
