@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--diag", default="auto", choices=["auto", "level2", "symbolic"])
     ap.add_argument("--cpu-n", type=int, default=6144, help="oracle sample size for cpu_baseline")
     ap.add_argument("--ref-n", type=int, default=4096, help="oracle sample size per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -228,7 +229,7 @@ def run_reference(args):
 
 def ours_config(args):
     return {"workload": f"chol_rev FP64 N={args.n}, SE covariance ell 0.3 on [0,1]^3 + 1e-4 I (seed {SE_SEED})",
-            "n": args.n, "nb": args.nb or "default",
+            "n": args.n, "nb": args.nb or "default", "diag": args.diag,
             "step": "chol_fwd -> chol_fwd_sens -> chol_rev on one N x N problem",
             "l2": "inputs exceed L2 (512 MiB per FP64 matrix at N=8192); no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
@@ -267,9 +268,9 @@ def run_ours(args):
         ev[0].record(stream)
         info = cd.chol_fwd(A, nb=nb, prec=prec)
         ev[1].record(stream)
-        cd.chol_fwd_sens(A, Ad, nb=nb, prec=prec)
+        cd.chol_fwd_sens(A, Ad, nb=nb, prec=prec, diag=args.diag)
         ev[2].record(stream)
-        cd.chol_rev(A, Ab, nb=nb, prec=prec)
+        cd.chol_rev(A, Ab, nb=nb, prec=prec, diag=args.diag)
         ev[3].record(stream)
         return ev, info
 

@@ -90,10 +90,20 @@ typedef enum {
   CD_OUT_SYM = 1   /* full symmetric Sigma_bar of Eq. symrev                   */
 } cd_output;
 
+typedef enum {
+  CD_DIAG_AUTO = 0,     /* the faster on GB300: currently CD_DIAG_SYMBOLIC       */
+  CD_DIAG_LEVEL2 = 1,   /* one-CTA level-2 loop on the tile (Sec. 4.1)           */
+  CD_DIAG_SYMBOLIC = 2  /* Eq. symrevtril / Eq. symfwd as FP64 products with the
+                           diagonal block's inverse, spread over many CTAs     */
+} cd_diag;
+
 typedef struct {
   int nb;               /* block size N_b; 0 = library default                 */
   int prec;             /* a cd_precision value                                */
   int out;              /* a cd_output value (cd_chol_rev only)                */
+  int diag;             /* a cd_diag value: the diagonal-block routine of the
+                           reverse and forward-sensitivity passes (Sec. 4.2
+                           allows either; both give the exact result)        */
   long long spin_limit; /* bound on device-side wait iterations; 0 = default   */
 } cd_options;
 

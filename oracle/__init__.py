@@ -258,6 +258,62 @@ def gp_nlml_grad(theta, X, y):
     return np.array([float((Sbar * np.tril(dS)).sum()) for dS in gp_dsigma(theta, X)])
 
 
+# --------------------------------------------------------------------------
+# Column residuals of the defining equations: O(n^2) per column, so they pin
+# results at sizes where the full oracle would take minutes.
+# --------------------------------------------------------------------------
+
+def fwd_residual_columns(sigma, L, cols):
+    """max_q ||(L L^T)[:, q] - Sigma[:, q]|| / ||Sigma[:, q]|| over the given columns (Sec. 1: Sigma = L L^T)."""
+    L = np.tril(_f64(L))
+    S = np.tril(_f64(sigma))
+    S = S + np.tril(S, -1).T
+    out = 0.0
+    for q in cols:
+        r = L @ L[q, :] - S[:, q]
+        out = max(out, float(np.linalg.norm(r) / np.linalg.norm(S[:, q])))
+    return out
+
+
+def sens_residual_columns(sigma_dot, L, L_dot, cols):
+    """Eq. symfwd implies L_dot L^T + L L_dot^T = Sigma_dot: max over columns of
+    ||residual|| / (||L_dot|| ||L[q, :]|| + ||L|| ||L_dot[q, :]||)."""
+    L = np.tril(_f64(L))
+    Ld = np.tril(_f64(L_dot))
+    Sd = np.tril(_f64(sigma_dot))
+    Sd = Sd + np.tril(Sd, -1).T
+    nL, nLd = np.linalg.norm(L), np.linalg.norm(Ld)
+    out = 0.0
+    for q in cols:
+        r = Ld @ L[q, :] + L @ Ld[q, :] - Sd[:, q]
+        scale = nLd * np.linalg.norm(L[q, :]) + nL * np.linalg.norm(Ld[q, :])
+        out = max(out, float(np.linalg.norm(r) / scale))
+    return out
+
+
+def rev_residual_columns(L, L_bar, T, cols):
+    """Eq. symrevtril implies L^T (T + T^T) L = P + P^T with P = Phi(L^T L_bar),
+    T = tril(Sigma_bar): max over columns of ||residual|| / (||L|| ||(T + T^T) L[:, q]||)."""
+    L = np.tril(_f64(L))
+    Lb = np.tril(_f64(L_bar))
+    T = np.tril(_f64(T))
+    nL = np.linalg.norm(L)
+    out = 0.0
+    for q in cols:
+        v = L[:, q]
+        u = T @ v + T.T @ v
+        lhs = L.T @ u
+        colP = L.T @ Lb[:, q]            # column q of L^T L_bar
+        colP[:q] = 0.0
+        colP[q] *= 0.5
+        rowP = L[:, q] @ Lb              # row q of L^T L_bar
+        rowP[q + 1:] = 0.0
+        rowP[q] *= 0.5
+        rhs = colP + rowP
+        out = max(out, float(np.linalg.norm(lhs - rhs) / (nL * np.linalg.norm(u))))
+    return out
+
+
 def flops_rev(n: int) -> float:
     """Nominal flop count of one reverse pass, 2 n^3 / 3 (leading term)."""
     return 2.0 * n ** 3 / 3.0
@@ -268,5 +324,6 @@ __all__ = [
     "chol_unblocked", "chol_unblocked_fwd", "chol_unblocked_rev",
     "chol_symbolic_fwd", "chol_symbolic_rev", "sym_from_tril",
     "dchol_jacobian", "rel_fro", "gp_sigma", "gp_dsigma", "gp_nlml",
-    "gp_nlml_grad", "rbf_sqdist", "flops_rev",
+    "gp_nlml_grad", "rbf_sqdist", "flops_rev", "fwd_residual_columns", "sens_residual_columns",
+    "rev_residual_columns",
 ]

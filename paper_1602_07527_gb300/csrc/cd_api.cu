@@ -63,7 +63,8 @@ int nblocks(int n, int nb) { return (n + nb - 1) / nb; }
 // Workspace one problem of size n needs at one recursion level.
 size_t prob_bytes(int n, int nb) {
   if (n <= 0) return 0;
-  return align_up(sizeof(double) * (size_t)nblocks(n, nb) * nb * nb) + align_up(sizeof(double) * (size_t)n * nb);
+  return align_up(sizeof(double) * (size_t)nblocks(n, nb) * nb * nb) + align_up(sizeof(double) * (size_t)n * nb) +
+         2 * align_up(sizeof(double) * (size_t)nb * nb);
 }
 
 // Extra workspace of the recursive diagonal step (nb > kTileMax).
@@ -87,6 +88,7 @@ struct Prob {
     long long ldb, ldn;
     int pad, T;
   } mx;
+  double *T1, *T2;  // nb x nb temporaries of the symbolic diagonal step
 };
 
 // Per-launch event records of cd_profile_enable.
@@ -177,8 +179,8 @@ struct Ctx {
   }
 };
 
-const char *kAName[3] = {"N", "T", "SYM2"};
-const char *kBName[3] = {"N", "T", "TL"};
+const char *kAName[6] = {"N", "T", "SYM2", "TL", "SYM1", "NL"};
+const char *kBName[4] = {"N", "T", "TL", "NL"};
 
 // Accumulates GEMMs of one kind into a grouped launch.  The split-K factor
 // is chosen at flush time for the whole group so that the grid fills whole
@@ -241,7 +243,8 @@ struct GemmBatch {
   void launch_sub(GemmGroup &sub, bool red, double flops, double bytes, double rbytes) {
     if (sub.count == 0) return;
     char name[48];
-    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "");
+    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "",
+             g.phi ? "_phi" : "");
     c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(sub, st); });
     if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
   }
@@ -252,6 +255,7 @@ struct GemmBatch {
     sub.amode = g.amode;
     sub.bmode = g.bmode;
     sub.lower = g.lower;
+    sub.phi = g.phi;
     size_t used = 0;
     double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
@@ -360,6 +364,62 @@ TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double 
   return d;
 }
 
+// The diagonal routine of the reverse and forward-sensitivity passes.  Both
+// choices are exact (Sec. 4.2); the products spread the work over many CTAs
+// and measure faster on GB300 in both precisions, so they are the default.
+bool diag_symbolic(const Ctx &c) {
+  const int d = c.opt ? c.opt->diag : CD_DIAG_AUTO;
+  return d != CD_DIAG_LEVEL2;
+}
+
+// One block of the reverse pass's diagonal step, Eq. symrevtril on the block:
+// D_bar <- Phi(D^{-T} (P + P^T) D^{-1}),  P = Phi(D^T D_bar), with D^{-1} the
+// precomputed inverse of the block (full storage, zeros above the diagonal).
+struct DiagRev {
+  const double *D;
+  long long ldd;
+  double *Db;
+  long long lddb;
+  const double *Dinv;
+  double *T1, *T2;
+  int w, ldt;
+};
+void rev_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
+  {  // P = Phi(D^T D_bar)
+    GemmBatch gb(c, A_TL, B_NL, true);
+    gb.g.phi = 1;
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.D, x.ldd, x.Db, x.lddb, nullptr, 0, x.T1, x.ldt, 1.0, 0.0);
+  }
+  {  // Y = (P + P^T) D^{-1}
+    GemmBatch gb(c, A_SYM2, B_N, false);
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.T1, x.ldt, x.Dinv, x.ldt, nullptr, 0, x.T2, x.ldt, 1.0, 0.0);
+  }
+  {  // D_bar = Phi(D^{-T} Y)
+    GemmBatch gb(c, A_T, B_N, true);
+    gb.g.phi = 1;
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.Dinv, x.ldt, x.T2, x.ldt, nullptr, 0, x.Db, x.lddb, 1.0, 0.0);
+  }
+}
+
+// One block of the forward-sensitivity diagonal step, Eq. symfwd on the block:
+// D_dot <- D Phi(D^{-1} S D^{-T}), S the symmetric block whose lower triangle
+// is D_dot.
+void sens_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
+  {  // Z = S D^{-T}
+    GemmBatch gb(c, A_SYM1, B_T, false);
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.Db, x.lddb, x.Dinv, x.ldt, nullptr, 0, x.T1, x.ldt, 1.0, 0.0);
+  }
+  {  // X = Phi(D^{-1} Z)
+    GemmBatch gb(c, A_N, B_N, true);
+    gb.g.phi = 1;
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.Dinv, x.ldt, x.T1, x.ldt, nullptr, 0, x.T2, x.ldt, 1.0, 0.0);
+  }
+  {  // D_dot = D X
+    GemmBatch gb(c, A_NL, B_NL, true);
+    for (auto &x : v) gb.add(x.w, x.w, x.w, x.D, x.ldd, x.T2, x.ldt, nullptr, 0, x.Db, x.lddb, 1.0, 0.0);
+  }
+}
+
 // Forward declarations (recursive diagonal steps).
 void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
@@ -426,10 +486,13 @@ bool bind_workspace(std::vector<Prob> &P, int nb, Arena &ar) {
   for (auto &p : P) {
     p.dinv = nullptr;
     p.W = nullptr;
+    p.T1 = p.T2 = nullptr;
     if (p.n <= 0) continue;
     p.dinv = (double *)ar.take(sizeof(double) * (size_t)nblocks(p.n, nb) * nb * nb);
     p.W = (double *)ar.take(sizeof(double) * (size_t)p.n * nb);
-    if (!p.dinv || !p.W) return false;
+    p.T1 = (double *)ar.take(sizeof(double) * (size_t)nb * nb);
+    p.T2 = (double *)ar.take(sizeof(double) * (size_t)nb * nb);
+    if (!p.dinv || !p.W || !p.T1 || !p.T2) return false;
   }
   return true;
 }
@@ -557,6 +620,16 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         gb.add(w, w, m, p.W, nb, p.L + (long long)k * p.ldl + j, p.ldl, Db, p.ldx, Db, p.ldx, -1.0, 1.0);
       }
     }
+    if (diag_symbolic(c)) {  // r4 as the products of Eq. symrevtril
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, k - j, nb});
+      }
+      rev_diag_symbolic(c, v);
+    } else
     {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)
       TileBatch tb(c, T_REV);
       for (auto &p : P) {
@@ -631,6 +704,17 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           gb.add(w, w, j, R, p.ldl, Rd, p.ldx, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
       }
     }
+    if (diag_symbolic(c)) {  // g2 as the products of Eq. symfwd
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
+      }
+      sens_diag_symbolic(c, v);
+    } else
     {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
       TileBatch tb(c, T_SENS);
       for (auto &p : P) {
@@ -953,6 +1037,16 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                p.ldx, Db, p.ldx, -1.0, 1.0);
       }
     }
+    if (diag_symbolic(c)) {  // r4 as the products of Eq. symrevtril
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, k - j, nb});
+      }
+      rev_diag_symbolic(c, v);
+    } else
     {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)   (FP64)
       TileBatch tb(c, T_REV);
       for (auto &p : P) {
@@ -1130,6 +1224,17 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                1.0);
       }
     }
+    if (diag_symbolic(c)) {  // g2 as the products of Eq. symfwd
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
+      }
+      sens_diag_symbolic(c, v);
+    } else
     {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
       TileBatch tb(c, T_SENS);
       for (auto &p : P) {
@@ -1247,7 +1352,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   cd_options_default(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.nb < 0 || opt.prec < CD_FP64 || opt.prec > CD_MIXED_BF16X6 || opt.out < CD_OUT_TRIL ||
-      opt.out > CD_OUT_SYM)
+      opt.out > CD_OUT_SYM || opt.diag < CD_DIAG_AUTO || opt.diag > CD_DIAG_SYMBOLIC)
     return CD_EINVAL;
   int nmax = 0;
   for (int b = 0; b < batch; ++b) {
@@ -1347,6 +1452,7 @@ int rev_in_scratch(int n, const double *L, long long ldl, double *Abar, long lon
   cd_options_default(&opt);
   opt.nb = nb;
   opt.out = out;
+  opt.diag = CD_DIAG_LEVEL2;
   std::vector<Prob> P(1);
   P[0] = Prob{n, L, ldl, Abar, lda, nullptr, nullptr, nullptr, 0};
   if (!bind_workspace(P, nb, ar)) return CD_EINVAL;
@@ -1372,6 +1478,7 @@ void cd_options_default(cd_options *opt) {
   opt->nb = 0;
   opt->prec = CD_FP64;
   opt->out = CD_OUT_TRIL;
+  opt->diag = CD_DIAG_AUTO;
   opt->spin_limit = 0;
 }
 

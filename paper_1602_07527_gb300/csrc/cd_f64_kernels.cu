@@ -24,6 +24,9 @@ template <int AM>
 __device__ __forceinline__ double load_a(const double *__restrict__ A, long long lda, int i, int k) {
   if (AM == A_N) return A[(long long)i * lda + k];
   if (AM == A_T) return A[(long long)k * lda + i];
+  if (AM == A_TL) return k >= i ? A[(long long)k * lda + i] : 0.0;
+  if (AM == A_NL) return i >= k ? A[(long long)i * lda + k] : 0.0;
+  if (AM == A_SYM1) return i >= k ? A[(long long)i * lda + k] : A[(long long)k * lda + i];
   if (i > k) return A[(long long)i * lda + k];
   if (i < k) return A[(long long)k * lda + i];
   return 2.0 * A[(long long)i * lda + i];
@@ -33,6 +36,7 @@ template <int BM>
 __device__ __forceinline__ double load_b(const double *__restrict__ B, long long ldb, int k, int j) {
   if (BM == B_N) return B[(long long)k * ldb + j];
   if (BM == B_T) return B[(long long)j * ldb + k];
+  if (BM == B_NL) return k >= j ? B[(long long)k * ldb + j] : 0.0;
   return (j >= k) ? B[(long long)j * ldb + k] : 0.0;
 }
 
@@ -121,6 +125,7 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
       if (j >= N || (LOWER && j > i)) continue;
       if (d.splits == 1) {
         double v = alpha * acc[r][c];
+        if (LOWER && g.phi && i == j) v *= 0.5;
         if (beta != 0.0) v = fma(beta, d.Cin[(long long)i * d.ldcin + j], v);
         d.Cout[(long long)i * d.ldcout + j] = v;
       } else {
@@ -142,6 +147,7 @@ __global__ void k_reduce_f64(const __grid_constant__ GemmGroup g) {
     if (LOWER && j > i) continue;
     double s = 0.0;
     for (int z = 0; z < d.splits; ++z) s += d.part[(long long)z * total + e];
+    if (LOWER && g.phi && i == j) s *= 0.5;
     if (d.beta != 0.0) s = fma(d.beta, d.Cin[(long long)i * d.ldcin + j], s);
     d.Cout[(long long)i * d.ldcout + j] = s;
   }
@@ -158,12 +164,16 @@ static cudaError_t launch_gemm_ab(const GemmGroup &g, cudaStream_t s) {
 
 cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s) {
   if (g.count <= 0 || g.total_tiles <= 0) return cudaSuccess;
-  switch (g.amode * 3 + g.bmode) {
-    case A_N * 3 + B_N: return launch_gemm_ab<A_N, B_N>(g, s);
-    case A_N * 3 + B_T: return launch_gemm_ab<A_N, B_T>(g, s);
-    case A_N * 3 + B_TL: return launch_gemm_ab<A_N, B_TL>(g, s);
-    case A_T * 3 + B_N: return launch_gemm_ab<A_T, B_N>(g, s);
-    case A_SYM2 * 3 + B_N: return launch_gemm_ab<A_SYM2, B_N>(g, s);
+  switch (g.amode * 8 + g.bmode) {
+    case A_N * 8 + B_N: return launch_gemm_ab<A_N, B_N>(g, s);
+    case A_N * 8 + B_T: return launch_gemm_ab<A_N, B_T>(g, s);
+    case A_N * 8 + B_TL: return launch_gemm_ab<A_N, B_TL>(g, s);
+    case A_T * 8 + B_N: return launch_gemm_ab<A_T, B_N>(g, s);
+    case A_SYM2 * 8 + B_N: return launch_gemm_ab<A_SYM2, B_N>(g, s);
+    // symbolic diagonal steps (Eqs. symrevtril, symfwd)
+    case A_TL * 8 + B_NL: return launch_gemm_ab<A_TL, B_NL>(g, s);
+    case A_SYM1 * 8 + B_T: return launch_gemm_ab<A_SYM1, B_T>(g, s);
+    case A_NL * 8 + B_NL: return launch_gemm_ab<A_NL, B_NL>(g, s);
     default: return cudaErrorInvalidValue;
   }
 }

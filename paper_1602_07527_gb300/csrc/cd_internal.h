@@ -12,16 +12,20 @@ namespace cd {
 // Grouped FP64 GEMM: Cout = beta * Cin + alpha * op(A) op(B), for up to
 // kMaxGemm independent problems per launch (batched work shares one grid).
 // ---------------------------------------------------------------------------
-enum AMode { A_N = 0, A_T = 1, A_SYM2 = 2 };
+enum AMode { A_N = 0, A_T = 1, A_SYM2 = 2, A_TL = 3, A_SYM1 = 4, A_NL = 5 };
 // A_N   : a(i,k) = A[i*lda + k]
 // A_T   : a(i,k) = A[k*lda + i]
 // A_SYM2: a(i,k) = symmetric view of a lower-stored matrix with doubled
 //         diagonal: A[i][k] (i > k), A[k][i] (i < k), 2 A[i][i] (i == k).
 //         This is G = X + X^T for X = tril(A), used by the reverse pass.
-enum BMode { B_N = 0, B_T = 1, B_TL = 2 };
+// A_TL  : a(i,k) = A[k][i] if k >= i else 0   (transpose of a lower matrix)
+// A_SYM1: a(i,k) = A[i][k] (i >= k), A[k][i] (i < k): symmetric view of a lower-stored matrix
+// A_NL  : a(i,k) = A[i][k] if i >= k else 0   (lower matrix, upper storage ignored)
+enum BMode { B_N = 0, B_T = 1, B_TL = 2, B_NL = 3 };
 // B_N   : b(k,j) = B[k*ldb + j]
 // B_T   : b(k,j) = B[j*ldb + k]
 // B_TL  : b(k,j) = B[j*ldb + k] if j >= k else 0   (transpose of a lower matrix)
+// B_NL  : b(k,j) = B[k*ldb + j] if k >= j else 0   (lower matrix, upper storage ignored)
 
 struct GemmDesc {
   const double *A, *B, *Cin;
@@ -35,7 +39,7 @@ struct GemmDesc {
 constexpr int kMaxGemm = 32;
 struct GemmGroup {
   int count, total_tiles;
-  int amode, bmode, lower, pad_;
+  int amode, bmode, lower, phi;  // phi: halve the diagonal of a lower output (Eq. phi)
   GemmDesc d[kMaxGemm];
 };
 

@@ -20,6 +20,7 @@ _ERR = {CD_EINVAL: "invalid argument", CD_ENOMEM: "workspace allocation failed",
         CD_ECUDA: "CUDA error", CD_ETIMEOUT: "device-side wait timed out",
         CD_ESCRATCH: "problem larger than the fixed scratch of cd_chol_rev_noalloc"}
 PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+DIAG = {"auto": 0, "level2": 1, "symbolic": 2}
 OUT = {"tril": 0, "sym": 1}
 
 
@@ -35,7 +36,7 @@ class KernelStat(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int),
+    _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int), ("diag", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong)]
 
 
@@ -152,10 +153,11 @@ def _h(handle_, device):
     return handle_.ptr if isinstance(handle_, Handle) else handle_
 
 
-def options(nb=0, prec="fp64", out="tril", spin_limit=0):
+def options(nb=0, prec="fp64", out="tril", spin_limit=0, diag="auto"):
     o = Options()
     lib().cd_options_default(ctypes.byref(o))
     o.nb = int(nb)
+    o.diag = DIAG[diag] if isinstance(diag, str) else int(diag)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.out = OUT[out] if isinstance(out, str) else int(out)
     o.spin_limit = int(spin_limit)
@@ -197,25 +199,25 @@ def chol_fwd(A, nb=0, prec="fp64", info=None, handle_=None):
     return info
 
 
-def chol_rev(L, Abar, nb=0, prec="fp64", out="tril", handle_=None):
+def chol_rev(L, Abar, nb=0, prec="fp64", out="tril", handle_=None, diag="auto"):
     """In place: tril(Abar) = L_bar -> tril(Sigma_bar) (Sec. 4.2 chol_blocked_rev)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Abar, "Abar")
     if n != n2 or L.device != Abar.device:
         raise ValueError("L and Abar must have the same size and device")
-    o = options(nb, prec, out)
+    o = options(nb, prec, out, diag=diag)
     _check(lib().cd_chol_rev(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Abar.data_ptr()), lda,
                              ctypes.byref(o), _stream(L.device)), "cd_chol_rev")
     return Abar
 
 
-def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None):
+def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None, diag="auto"):
     """In place: tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.2 chol_blocked_fwd)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Adot, "Adot")
     if n != n2 or L.device != Adot.device:
         raise ValueError("L and Adot must have the same size and device")
-    o = options(nb, prec)
+    o = options(nb, prec, diag=diag)
     _check(lib().cd_chol_fwd_sens(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Adot.data_ptr()), lda,
                                   ctypes.byref(o), _stream(L.device)), "cd_chol_fwd_sens")
     return Adot
@@ -245,7 +247,7 @@ def chol_fwd_batched(As, nb=0, prec="fp64", info=None, handle_=None):
     return info
 
 
-def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None):
+def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None, diag="auto"):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Abars, "Abar")
     if b != b2 or ns != ns2:
@@ -253,13 +255,13 @@ def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None):
     if b == 0:
         return Abars
     dev = Ls[0].device
-    o = options(nb, prec, out)
+    o = options(nb, prec, out, diag=diag)
     _check(lib().cd_chol_rev_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_rev_batched")
     return Abars
 
 
-def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None):
+def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None, diag="auto"):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Adots, "Adot")
     if b != b2 or ns != ns2:
@@ -267,7 +269,7 @@ def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None):
     if b == 0:
         return Adots
     dev = Ls[0].device
-    o = options(nb, prec)
+    o = options(nb, prec, diag=diag)
     _check(lib().cd_chol_fwd_sens_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_fwd_sens_batched")
     return Adots

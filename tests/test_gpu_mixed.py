@@ -108,3 +108,16 @@ def test_mixed_batched_ragged(cd):
         assert torch.equal(As[i], a1) and torch.equal(Abs[i], r1)   # batched == alone, bitwise
         assert oracle.rel_fro(As[i].cpu().numpy(), c[1]) <= OPS_TOL["bf16x6"]
         assert oracle.rel_fro(Abs[i].cpu().numpy(), oracle.chol_unblocked_rev(c[1], c[2])) <= OPS_TOL["bf16x6"]
+
+
+def test_mixed_with_level2_diagonal(cd):
+    n, nb = 333, 64
+    S, L, Lb, Sd = _case(n, 1200)
+    Ld = torch.tensor(L, device=DEV)
+    Ab = torch.tensor(Lb, device=DEV)
+    cd.chol_rev(Ld, Ab, nb=nb, prec="bf16x6", diag="level2")
+    Ad = torch.tensor(np.tril(Sd), device=DEV)
+    cd.chol_fwd_sens(Ld, Ad, nb=nb, prec="bf16x6", diag="level2")
+    torch.cuda.synchronize()
+    assert oracle.rel_fro(Ab.cpu().numpy(), oracle.chol_unblocked_rev(L, Lb)) <= OPS_TOL["bf16x6"]
+    assert oracle.rel_fro(Ad.cpu().numpy(), oracle.chol_unblocked_fwd(L, Sd)) <= OPS_TOL["bf16x6"]

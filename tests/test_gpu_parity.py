@@ -206,3 +206,35 @@ def test_launch_count_increases(cd):
     _, L, Lb, _ = case(96, 900)
     cd.chol_rev(dev(L), dev(Lb), nb=32)
     assert cd.launch_count() > before
+
+
+@pytest.mark.parametrize("n,nb", [(1, 64), (2, 64), (33, 16), (129, 128), (300, 128), (333, 96), (600, 256)])
+def test_symbolic_diagonal_step_matches_oracle(cd, n, nb):
+    """The diagonal routine as the products of Eq. symrevtril / Eq. symfwd
+    (the paper's alternative to the level-2 loop) gives the same result."""
+    _, L, Lb, Sd = case(n, 950 + n)
+    Ab = dev(Lb)
+    cd.chol_rev(dev(L), Ab, nb=nb, diag="symbolic")
+    assert oracle.rel_fro(host(Ab), oracle.chol_unblocked_rev(L, Lb)) <= TOL
+    Ad = dev(np.tril(Sd))
+    cd.chol_fwd_sens(dev(L), Ad, nb=nb, diag="symbolic")
+    assert oracle.rel_fro(host(Ad), oracle.chol_unblocked_fwd(L, Sd)) <= TOL
+
+
+def test_symbolic_diagonal_leaves_upper_untouched(cd):
+    n, nb = 200, 64
+    _, L, Lb, Sd = case(n, 990)
+    pad = 3
+    upper = np.triu(np.ones((n, n + pad), dtype=bool), 1)
+    Lp = dev(_poison_upper(L, pad))[:, :n]
+    for kind in ("rev", "sens"):
+        buf = dev(_poison_upper(Lb if kind == "rev" else Sd, pad))
+        if kind == "rev":
+            cd.chol_rev(Lp, buf[:, :n], nb=nb, diag="symbolic")
+            ref = oracle.chol_unblocked_rev(L, Lb)
+        else:
+            cd.chol_fwd_sens(Lp, buf[:, :n], nb=nb, diag="symbolic")
+            ref = oracle.chol_unblocked_fwd(L, Sd)
+        out = host(buf)
+        assert np.all(np.isnan(out[upper])), kind
+        assert oracle.rel_fro(np.tril(out[:, :n]), ref) <= TOL, kind

@@ -281,3 +281,29 @@ def test_gp_gradient_textbook_and_fd(oracle):
     # the likelihood itself against a library log-determinant and solve
     sign, logdet = np.linalg.slogdet(S)
     assert abs(oracle.gp_nlml(theta, X, y) - (0.5 * y @ alpha + 0.5 * logdet)) <= 1e-10 * abs(logdet)
+
+
+# -- column residuals used to check full-size results ------------------------
+
+@pytest.mark.parametrize("n", [7, 90])
+def test_column_residuals_accept_exact_and_reject_perturbed(oracle, n):
+    S = wishart(n, seed=30)
+    L, _ = oracle.chol_unblocked(S)
+    Lb = W.lbar(n, 30)
+    Sd = W.sigma_dot(n, 30)
+    T = oracle.chol_unblocked_rev(L, Lb)
+    Ld = oracle.chol_unblocked_fwd(L, Sd)
+    cols = list(range(0, n, max(1, n // 6)))
+    assert oracle.fwd_residual_columns(S, L, cols) <= 1e-14
+    assert oracle.sens_residual_columns(Sd, L, Ld, cols) <= 1e-14
+    assert oracle.rev_residual_columns(L, Lb, T, cols) <= 1e-14
+    # a relative perturbation of 1e-9 anywhere in the checked columns' reach is visible
+    E = np.zeros((n, n))
+    E[n - 1, cols[-1]] = 1e-9 * np.max(np.abs(T))
+    assert oracle.rev_residual_columns(L, Lb, T + E, cols) > 1e-12
+    E = np.zeros((n, n))
+    E[n - 1, cols[-1]] = 1e-9 * np.max(np.abs(Ld))
+    assert oracle.sens_residual_columns(Sd, L, Ld + E, cols) > 1e-12
+    E = np.zeros((n, n))
+    E[n - 1, cols[-1]] = 1e-9 * np.max(np.abs(L))
+    assert oracle.fwd_residual_columns(S, L + E, cols) > 1e-12
