@@ -51,10 +51,17 @@ struct Arena {
   }
 };
 
-int pick_nb(int n, const cd_options *opt) {
+// Default block sizes (measured on GB300).  FP64 passes are DFMA-bound and
+// insensitive to nb; split-BF16 reverse and forward-sensitivity passes are
+// bound by their sequence of steps and run fastest with 256-wide blocks at
+// large n; the split-BF16 factorisation is bound by its one-CTA diagonal
+// factorisations and prefers 128.
+int pick_nb(int n, const cd_options *opt, bool factorisation = false) {
   int nb = (opt && opt->nb > 0) ? opt->nb : (n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall);
-  // the tensor-core path works on 64-wide K blocks: round its block size up
-  if (opt && opt->prec != CD_FP64) nb = (nb + 63) / 64 * 64;
+  if (opt && opt->prec != CD_FP64) {
+    if (opt->nb <= 0 && n >= 4096 && !factorisation) nb = 256;
+    nb = (nb + 63) / 64 * 64;  // the tensor-core path works on 64-wide K blocks
+  }
   return nb;
 }
 
@@ -365,10 +372,15 @@ TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double 
 }
 
 // The diagonal routine of the reverse and forward-sensitivity passes.  Both
-// choices are exact (Sec. 4.2); the products spread the work over many CTAs
-// and measure faster on GB300 in both precisions, so they are the default.
-bool diag_symbolic(const Ctx &c) {
+// choices are exact (Sec. 4.2).  The products spread one block's work over
+// many CTAs and measure faster on GB300 for multi-block problems; a problem
+// that is a single tile (no panel work to overlap) is faster as one level-2
+// CTA, batched with the others in one launch, and needs no block inverse.
+// The choice depends on the problem alone, so a problem computes the same
+// bits alone or batched.
+bool diag_symbolic(const Ctx &c, const Prob &p, int nb) {
   const int d = c.opt ? c.opt->diag : CD_DIAG_AUTO;
+  if (d == CD_DIAG_AUTO) return !(p.n <= nb && p.n <= kTileMax);
   return d != CD_DIAG_LEVEL2;
 }
 
@@ -458,27 +470,67 @@ void trtri_big(Ctx &c, const double *D, long long ldd, double *inv, long long ld
 // rev_partition: blocks [max(0,k-nb), k) for k = n, n-nb, ... (short block
 // first); otherwise [j, min(n, j+nb)) (short block last).
 void precompute_dinv(Ctx &c, std::vector<Prob> &P, int nb, bool rev_partition, Arena &ar) {
-  TileBatch tb(c, T_TRTRI);
-  for (auto &p : P) {
-    const int nbk = nblocks(p.n, nb);
-    for (int s = 0; s < nbk; ++s) {
-      int j, k;
-      if (rev_partition) {
-        k = p.n - s * nb;
-        j = std::max(0, k - nb);
-      } else {
-        j = s * nb;
-        k = std::min(p.n, j + nb);
-      }
-      const int w = k - j;
-      double *inv = p.dinv + (size_t)s * nb * nb;
-      if (w <= kTileMax) {
-        tb.add(tdesc(p.L + (long long)j * p.ldl + j, p.ldl, nullptr, 0, inv, nb, w));
-      } else {
-        tb.flush();
-        trtri_big(c, p.L + (long long)j * p.ldl + j, p.ldl, inv, nb, w, ar);
+  struct Blk {
+    const double *D;
+    long long ldd;
+    double *inv;
+    int w;
+  };
+  std::vector<Blk> two;  // kTileMax < w <= 2 kTileMax: one level of 2 x 2 blocking, batched
+  {
+    TileBatch tb(c, T_TRTRI);
+    for (auto &p : P) {
+      // the inverses serve the panel solves and the symbolic diagonal step only
+      if (p.n <= nb && !diag_symbolic(c, p, nb)) continue;
+      const int nbk = nblocks(p.n, nb);
+      for (int s = 0; s < nbk; ++s) {
+        int j, k;
+        if (rev_partition) {
+          k = p.n - s * nb;
+          j = std::max(0, k - nb);
+        } else {
+          j = s * nb;
+          k = std::min(p.n, j + nb);
+        }
+        const int w = k - j;
+        double *inv = p.dinv + (size_t)s * nb * nb;
+        const double *D = p.L + (long long)j * p.ldl + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(D, p.ldl, nullptr, 0, inv, nb, w));
+        } else if (w <= 2 * kTileMax && 2 * ((w / 2 + 63) / 64 * 64) <= nb) {
+          const int h1 = (w / 2 + 63) / 64 * 64;
+          tb.add(tdesc(D, p.ldl, nullptr, 0, inv, nb, h1));
+          tb.add(tdesc(D + (long long)h1 * p.ldl + h1, p.ldl, nullptr, 0, inv + (long long)h1 * nb + h1, nb, w - h1));
+          two.push_back({D, p.ldl, inv, w});
+        } else {
+          tb.flush();
+          trtri_big(c, D, p.ldl, inv, nb, w, ar);
+        }
       }
     }
+  }
+  if (two.empty()) return;
+  // [D11 0; D21 D22]^{-1} = [inv11 0; -inv22 D21 inv11  inv22]; the scratch
+  // T = D21 inv11 (h2 x h1, h2 <= h1, 2 h1 <= nb) of every block goes to the
+  // top-right quarter of its own nb x nb inverse buffer, cleared afterwards.
+  {
+    GemmBatch gb(c, A_N, B_N, false);
+    for (auto &b : two) {
+      const int h1 = (b.w / 2 + 63) / 64 * 64, h2 = b.w - h1;
+      gb.add(h2, h1, h1, b.D + (long long)h1 * b.ldd, b.ldd, b.inv, nb, nullptr, 0, b.inv + h1, nb, 1.0, 0.0);
+    }
+  }
+  {
+    GemmBatch gb(c, A_N, B_N, false);
+    for (auto &b : two) {
+      const int h1 = (b.w / 2 + 63) / 64 * 64, h2 = b.w - h1;
+      gb.add(h2, h1, h2, b.inv + (long long)h1 * nb + h1, nb, b.inv + h1, nb, nullptr, 0, b.inv + (long long)h1 * nb,
+             nb, -1.0, 0.0);
+    }
+  }
+  for (auto &b : two) {  // clear the top-right quarter (and the scratch beyond it) to zero
+    const int h1 = (b.w / 2 + 63) / 64 * 64;
+    c.cuda(cudaMemset2DAsync(b.inv + h1, sizeof(double) * nb, 0, sizeof(double) * (nb - h1), h1, c.s));
   }
 }
 
@@ -525,15 +577,17 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         gb.add(w, w, j, R, p.ldx, R, p.ldx, R + j, p.ldx, R + j, p.ldx, -1.0, 1.0);
       }
     }
-    {  // f2: D <- chol_unblocked(D); inverse of D for f4
+    {  // f2: D <- chol_unblocked(D); then the inverse of D for f4
       TileBatch tb(c, T_POTF2);
+      TileBatch ti(c, T_TRTRI);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, p.dinv, nb, w, p.info, p.col0 + j));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
+          if (k < p.n) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -545,6 +599,8 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
+      tb.flush();  // the factorisations first, then the inverses of their results
+      ti.flush();
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}   (W = C Dinv^T, then copy back)
@@ -620,21 +676,21 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         gb.add(w, w, m, p.W, nb, p.L + (long long)k * p.ldl + j, p.ldl, Db, p.ldx, Db, p.ldx, -1.0, 1.0);
       }
     }
-    if (diag_symbolic(c)) {  // r4 as the products of Eq. symrevtril
+    {  // r4 as the products of Eq. symrevtril (problems that use them)
       std::vector<DiagRev> v;
       for (auto &p : P) {
         int j, k;
-        if (!blk(p, s, j, k)) continue;
+        if (!blk(p, s, j, k) || !diag_symbolic(c, p, nb)) continue;
         v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
                      p.dinv + (size_t)s * nb * nb, p.T1, p.T2, k - j, nb});
       }
-      rev_diag_symbolic(c, v);
-    } else
+      if (!v.empty()) rev_diag_symbolic(c, v);
+    }
     {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)
       TileBatch tb(c, T_REV);
       for (auto &p : P) {
         int j, k;
-        if (!blk(p, s, j, k)) continue;
+        if (!blk(p, s, j, k) || diag_symbolic(c, p, nb)) continue;
         const int w = k - j;
         const double *D = p.L + (long long)j * p.ldl + j;
         double *Db = p.X + (long long)j * p.ldx + j;
@@ -704,22 +760,22 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           gb.add(w, w, j, R, p.ldl, Rd, p.ldx, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
       }
     }
-    if (diag_symbolic(c)) {  // g2 as the products of Eq. symfwd
+    {  // g2 as the products of Eq. symfwd (problems that use them)
       std::vector<DiagRev> v;
       for (auto &p : P) {
         const int j = s * nb;
-        if (j >= p.n) continue;
+        if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
         const int w = std::min(p.n, j + nb) - j;
         v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
                      p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
       }
-      sens_diag_symbolic(c, v);
-    } else
+      if (!v.empty()) sens_diag_symbolic(c, v);
+    }
     {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
       TileBatch tb(c, T_SENS);
       for (auto &p : P) {
         const int j = s * nb;
-        if (j >= p.n) continue;
+        if (j >= p.n || diag_symbolic(c, p, nb)) continue;
         const int w = std::min(p.n, j + nb) - j;
         const double *D = p.L + (long long)j * p.ldl + j;
         double *Dd = p.X + (long long)j * p.ldx + j;
@@ -1037,21 +1093,21 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                p.ldx, Db, p.ldx, -1.0, 1.0);
       }
     }
-    if (diag_symbolic(c)) {  // r4 as the products of Eq. symrevtril
+    {  // r4 as the products of Eq. symrevtril (problems that use them)
       std::vector<DiagRev> v;
       for (auto &p : P) {
         int j, k;
-        if (!blk(p, s, j, k)) continue;
+        if (!blk(p, s, j, k) || !diag_symbolic(c, p, nb)) continue;
         v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
                      p.dinv + (size_t)s * nb * nb, p.T1, p.T2, k - j, nb});
       }
-      rev_diag_symbolic(c, v);
-    } else
+      if (!v.empty()) rev_diag_symbolic(c, v);
+    }
     {  // r4: D_bar <- chol_unblocked_rev(D, D_bar)   (FP64)
       TileBatch tb(c, T_REV);
       for (auto &p : P) {
         int j, k;
-        if (!blk(p, s, j, k)) continue;
+        if (!blk(p, s, j, k) || diag_symbolic(c, p, nb)) continue;
         const int w = k - j;
         const double *D = p.L + (long long)j * p.ldl + j;
         double *Db = p.X + (long long)j * p.ldx + j;
@@ -1124,15 +1180,17 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                p.ldx, -1.0, 1.0);
       }
     }
-    {  // f2: D <- chol_unblocked(D) and D^{-1}   (FP64)
+    {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
       TileBatch tb(c, T_POTF2);
+      TileBatch ti(c, T_TRTRI);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, p.dinv, nb, w, p.info, p.col0 + j));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
+          if (j + w < p.n) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -1144,6 +1202,8 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
+      tb.flush();  // the factorisations first, then the inverses of their results
+      ti.flush();
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}
@@ -1224,22 +1284,22 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                1.0);
       }
     }
-    if (diag_symbolic(c)) {  // g2 as the products of Eq. symfwd
+    {  // g2 as the products of Eq. symfwd (problems that use them)
       std::vector<DiagRev> v;
       for (auto &p : P) {
         const int j = s * nb;
-        if (j >= p.n) continue;
+        if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
         const int w = std::min(p.n, j + nb) - j;
         v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
                      p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
       }
-      sens_diag_symbolic(c, v);
-    } else
+      if (!v.empty()) sens_diag_symbolic(c, v);
+    }
     {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
       TileBatch tb(c, T_SENS);
       for (auto &p : P) {
         const int j = s * nb;
-        if (j >= p.n) continue;
+        if (j >= p.n || diag_symbolic(c, p, nb)) continue;
         const int w = std::min(p.n, j + nb) - j;
         const double *D = p.L + (long long)j * p.ldl + j;
         double *Dd = p.X + (long long)j * p.ldx + j;
@@ -1370,7 +1430,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     if (cudaMemsetAsync(info, 0, sizeof(int) * batch, s) != cudaSuccess) return CD_ECUDA;
   }
   if (nmax == 0) return CD_OK;
-  const int nb = pick_nb(nmax, &opt);
+  const int nb = pick_nb(nmax, &opt, op == OP_FWD);
   size_t need = need_bytes(n, batch, nb);
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b) need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS);

@@ -228,53 +228,66 @@ __device__ void tile_store(const double *S, double *X, long long ldx, int t) {
     for (int j = lane; j <= i; j += 32) X[(long long)i * ldx + j] = S[pk(i, j)];
 }
 
-__device__ void tile_store_full(const double *S, double *X, long long ldx, int t) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < t; i += nw)
-    for (int j = lane; j < t; j += 32) X[(long long)i * ldx + j] = (j <= i) ? S[pk(i, j)] : 0.0;
+// Row of flat index e in the packed lower triangle (row r holds r + 1 entries).
+__device__ __forceinline__ int tri_row(int e) {
+  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  while (r * (r + 1) / 2 > e) --r;
+  return r;
 }
 
 // chol_unblocked (Sec. 4.1) on the tile, in right-looking order (the same
 // arithmetic as the paper's column loop, with each column's update applied
-// as soon as the column is final).  Returns the first 0-based column whose
-// pivot is not positive (or NaN), else -1.
-__device__ int dev_potf2(double *T, int t) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+// as soon as the column is final).  Per column: one thread forms the pivot's
+// square root and reciprocal; all threads scale the column by it; then the
+// rank-1 update of the trailing triangle is spread flat over all threads,
+// one FMA per element, so every warp is full.  cj holds the unscaled column
+// (double-buffered: the update writes the next column's values into cn).
+// Returns the first 0-based column whose pivot is not positive (or NaN), else -1.
+__device__ int dev_potf2(double *T, int t, double *cbuf, double *red) {
+  const int tid = threadIdx.x;
+  double *sc = cbuf + 2 * kTileMax;  // scaled column j
+  // flat index -> (row, column) of a trailing triangle, the same for every column
+  short2 *rc = reinterpret_cast<short2 *>(cbuf + 3 * kTileMax);
+  const int Emax = t * (t - 1) / 2;
+  for (int e = tid; e < Emax; e += blockDim.x) {
+    const int r = tri_row(e);
+    rc[e] = make_short2((short)r, (short)(e - r * (r + 1) / 2));
+  }
+  for (int i = tid; i < t; i += blockDim.x) cbuf[i] = T[pk(i, 0)];
+  __syncthreads();
   for (int j = 0; j < t; ++j) {
-    const double piv = T[pk(j, j)];
+    double *cj = cbuf + (j & 1) * kTileMax;
+    double *cn = cbuf + ((j + 1) & 1) * kTileMax;
+    if (tid == 0) {
+      const double piv = cj[j];
+      const bool ok = piv > 0.0;
+      const double dj = ok ? sqrt(piv) : 0.0;
+      red[0] = ok ? 1.0 / dj : 0.0;
+      red[1] = ok ? 1.0 : 0.0;
+      T[pk(j, j)] = ok ? dj : piv;
+    }
     __syncthreads();
-    if (!(piv > 0.0)) return j;
-    const double dj = sqrt(piv);
-    for (int i = j + 1 + tid; i < t; i += blockDim.x) T[pk(i, j)] /= dj;
-    if (tid == 0) T[pk(j, j)] = dj;
+    if (red[1] == 0.0) return j;
+    const double rd = red[0];
+    for (int i = j + 1 + tid; i < t; i += blockDim.x) {
+      const double v = cj[i] * rd;
+      sc[i] = v;
+      T[pk(i, j)] = v;
+    }
     __syncthreads();
-    for (int i = j + 1 + warp; i < t; i += nw) {
-      const double lij = T[pk(i, j)];
-      for (int k = j + 1 + lane; k <= i; k += 32) T[pk(i, k)] -= lij * T[pk(k, j)];
+    const int m = t - j - 1;
+    const int E = m * (m + 1) / 2;
+    for (int e = tid; e < E; e += blockDim.x) {
+      const short2 q = rc[e];
+      const int cc = q.y, i = j + 1 + q.x, k = j + 1 + cc;
+      const double v = fma(-sc[i], sc[k], T[pk(i, k)]);
+      T[pk(i, k)] = v;
+      if (cc == 0) cn[i] = v;
     }
     __syncthreads();
   }
   return -1;
-}
-
-// X = T^{-1} for lower T with nonzero diagonal, row by row (T X = I).
-__device__ void dev_trtri(const double *T, double *X, int t) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int P = t * (t + 1) / 2;
-  for (int e = tid; e < P; e += blockDim.x) X[e] = 0.0;
-  __syncthreads();
-  for (int i = tid; i < t; i += blockDim.x) X[pk(i, i)] = 1.0;
-  __syncthreads();
-  for (int k = 0; k < t; ++k) {
-    const double dk = T[pk(k, k)];
-    for (int c = tid; c <= k; c += blockDim.x) X[pk(k, c)] /= dk;
-    __syncthreads();
-    for (int i = k + 1 + warp; i < t; i += nw) {
-      const double tik = T[pk(i, k)];
-      for (int c = lane; c <= k; c += 32) X[pk(i, c)] -= tik * X[pk(k, c)];
-    }
-    __syncthreads();
-  }
 }
 
 // chol_unblocked_rev (Sec. 4.1) on the tile: column j from t-1 down to 0,
@@ -363,27 +376,10 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
     if (d.info != nullptr && *(volatile int *)d.info != 0) return;  // an earlier column failed
     tile_load(S0, d.X, d.ldx, t);
     __syncthreads();
-    const int bad = dev_potf2(S0, t);
+    const int bad = dev_potf2(S0, t, S1, red);
     __syncthreads();
     tile_store(S0, d.X, d.ldx, t);
-    if (bad >= 0) {
-      if (threadIdx.x == 0 && d.info != nullptr) *d.info = d.col0 + bad + 1;
-      if (d.inv != nullptr)
-        for (int e = threadIdx.x; e < t * t; e += blockDim.x)
-          d.inv[(long long)(e / t) * d.ldinv + (e % t)] = 0.0;
-      return;
-    }
-    if (d.inv != nullptr) {
-      dev_trtri(S0, S1, t);
-      __syncthreads();
-      tile_store_full(S1, d.inv, d.ldinv, t);
-    }
-  } else if (OP == T_TRTRI) {
-    tile_load(S0, d.L, d.ldl, t);
-    __syncthreads();
-    dev_trtri(S0, S1, t);
-    __syncthreads();
-    tile_store_full(S1, d.inv, d.ldinv, t);
+    if (bad >= 0 && threadIdx.x == 0 && d.info != nullptr) *d.info = d.col0 + bad + 1;
   } else {
     tile_load(S0, d.L, d.ldl, t);
     tile_load(S1, d.X, d.ldx, t);
@@ -397,6 +393,53 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
   }
 }
 
+// X = T^{-1} for a lower tile T (t <= 128): every column of X is an
+// independent forward substitution T x = e_c, so each warp computes one
+// column (lanes split the dot products, a shuffle tree sums them) and a tile
+// spreads over t / 8 CTAs.  Writes the full t x t inverse, zeros above.
+constexpr int kInvCols = 8;  // columns (warps) per CTA
+constexpr size_t kInvSmem = sizeof(double) * (kTileMax * (kTileMax + 1) / 2 + kTileMax + kInvCols * kTileMax);
+
+__global__ void __launch_bounds__(32 * kInvCols) k_trtri_cols(const __grid_constant__ TileGroup g) {
+  extern __shared__ double sm[];
+  const TileDesc &d = g.d[blockIdx.y];
+  const int t = d.t;
+  const int c0 = blockIdx.x * kInvCols;
+  if (t <= 0 || t > kTileMax || c0 >= t) return;
+  double *S = sm;                                       // packed tile
+  double *rdiag = sm + kTileMax * (kTileMax + 1) / 2;   // 1 / T_ii
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double *x = rdiag + kTileMax + warp * kTileMax;       // this warp's column
+  tile_load(S, d.L, d.ldl, t);
+  __syncthreads();
+  for (int i = threadIdx.x; i < t; i += blockDim.x) rdiag[i] = 1.0 / S[pk(i, i)];
+  __syncthreads();
+  const int c = c0 + warp;
+  if (c < t) {
+    for (int i = lane; i < c; i += 32) x[i] = 0.0;
+    if (lane == 0) x[c] = rdiag[c];
+    __syncwarp();
+    for (int i = c + 1; i < t; ++i) {
+      double s0 = 0.0;
+      for (int k = c + lane; k < i; k += 32) s0 = fma(S[pk(i, k)], x[k], s0);
+      s0 = warp_sum(s0);
+      if (lane == 0) x[i] = -s0 * rdiag[i];
+      __syncwarp();
+    }
+    for (int i = lane; i < t; i += 32) d.inv[(long long)i * d.ldinv + c] = x[i];
+  }
+}
+
+cudaError_t launch_trtri_group(const TileGroup &g, cudaStream_t s) {
+  if (g.count <= 0) return cudaSuccess;
+  int tmax = 0;
+  for (int p = 0; p < g.count; ++p) tmax = std::max(tmax, g.d[p].t);
+  if (tmax <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((tmax + kInvCols - 1) / kInvCols), (unsigned)g.count);
+  k_trtri_cols<<<grid, 32 * kInvCols, kInvSmem, s>>>(g);
+  return cudaGetLastError();
+}
+
 cudaError_t tile_kernels_init() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_tile<T_POTF2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
@@ -405,8 +448,7 @@ cudaError_t tile_kernels_init() {
     return e;
   if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_tile<T_TRTRI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
-    return e;
+  if ((e = cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem))) return e;
   return cudaSuccess;
 }
 
@@ -416,7 +458,7 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
     case T_POTF2: k_tile<T_POTF2><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_REV: k_tile<T_REV><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_SENS: k_tile<T_SENS><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
-    case T_TRTRI: k_tile<T_TRTRI><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
+    case T_TRTRI: return launch_trtri_group(g, s);
   }
   return cudaGetLastError();
 }

@@ -307,18 +307,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
     if (threadIdx.x == 0 && g.err) atomicExch(g.err, CD_ETIMEOUT);
     return;
   }
+  // Each thread owns one output column; rows go in chunks of 16 whose Cin
+  // values are all loaded before any is stored (Cin may alias Cout, and a
+  // thread only ever rewrites the elements it has read), so the loads of a
+  // chunk are in flight together instead of one global round trip per row.
   const int j = n0 + threadIdx.x;
   const double alpha = d.alpha, beta = d.beta;
-  for (int r = 0; r < BM; ++r) {
-    const int i = m0 + r;
-    if (i >= d.M) break;
-    if (j >= d.N || (LOWER && j > i)) continue;
-    double v = alpha * stage[r * LDS + threadIdx.x];
-    if (d.splits == 1) {
-      if (beta != 0.0) v = fma(beta, d.Cin[(long long)i * d.ldcin + j], v);
-      d.Cout[(long long)i * d.ldcout + j] = v;
-    } else {
-      d.part[((long long)z * d.M + i) * d.N + j] = v;
+  const bool col_ok = j < d.N;
+  const int rows = min(BM, d.M - m0);
+  constexpr int CH = 16;
+  for (int r0 = 0; r0 < rows; r0 += CH) {
+    double cin[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int r = r0 + q, i = m0 + r;
+      cin[q] = 0.0;
+      if (d.splits == 1 && beta != 0.0 && col_ok && r < rows && !(LOWER && j > i))
+        cin[q] = d.Cin[(long long)i * d.ldcin + j];
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int r = r0 + q, i = m0 + r;
+      if (!col_ok || r >= rows || (LOWER && j > i)) continue;
+      double v = alpha * stage[r * LDS + threadIdx.x];
+      if (d.splits == 1) {
+        if (beta != 0.0) v = fma(beta, cin[q], v);
+        d.Cout[(long long)i * d.ldcout + j] = v;
+      } else {
+        d.part[((long long)z * d.M + i) * d.N + j] = v;
+      }
     }
   }
 }

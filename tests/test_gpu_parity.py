@@ -238,3 +238,20 @@ def test_symbolic_diagonal_leaves_upper_untouched(cd):
         out = host(buf)
         assert np.all(np.isnan(out[upper])), kind
         assert oracle.rel_fro(np.tril(out[:, :n]), ref) <= TOL, kind
+
+
+@pytest.mark.parametrize("diag", ["auto", "level2", "symbolic"])
+def test_single_block_batches(cd, diag):
+    """Batches where every problem is one block (the serving case for small n)."""
+    sizes = [1, 7, 33, 64, 100, 128]
+    cases = [case(n, 1300 + n) for n in sizes]
+    Ls = [dev(c[1]) for c in cases]
+    Abs = [dev(c[2]) for c in cases]
+    Ads = [dev(np.tril(c[3])) for c in cases]
+    cd.chol_rev_batched(Ls, Abs, nb=128, diag=diag)
+    cd.chol_fwd_sens_batched(Ls, Ads, nb=128, diag=diag)
+    torch.cuda.synchronize()
+    for c, ab, ad in zip(cases, Abs, Ads):
+        _, L, Lb, Sd = c
+        assert oracle.rel_fro(host(ab), oracle.chol_unblocked_rev(L, Lb)) <= TOL
+        assert oracle.rel_fro(host(ad), oracle.chol_unblocked_fwd(L, Sd)) <= TOL
