@@ -275,9 +275,10 @@ struct GemmBatch {
         sp = (d.K + kchunk - 1) / kchunk;
       }
       const size_t mn = (size_t)d.M * d.N;
-      if (sp > 1 && (!part || mn * sp > part_cap)) {  // cannot split this one at all
-        sp = 1;
-        kchunk = std::max(d.K, 1);
+      if (sp > 1 && (!part || mn * sp > part_cap)) {  // as many splits as the partial region holds
+        sp = part ? (int)std::max<size_t>(1, part_cap / mn) : 1;
+        kchunk = sp > 1 ? ((d.K + sp - 1) / sp + 15) / 16 * 16 : std::max(d.K, 1);
+        if (sp > 1) sp = (d.K + kchunk - 1) / kchunk;
       }
       if (sp > 1 && used + mn * sp > part_cap) {  // buffer full: launch what we have first
         launch_sub(sub, red, flops, bytes, rbytes);
@@ -958,9 +959,10 @@ struct MixedBatch {
       int kchunk = ((kblocks + sp - 1) / sp) * 64;
       sp = (P.K + kchunk - 1) / kchunk;
       const size_t mn = (size_t)P.M * P.N;
-      if (sp > 1 && (!part || mn * sp > part_cap)) {
-        sp = 1;
-        kchunk = kblocks * 64;
+      if (sp > 1 && (!part || mn * sp > part_cap)) {  // as many splits as the partial region holds
+        sp = part ? (int)std::max<size_t>(1, part_cap / mn) : 1;
+        kchunk = ((kblocks + sp - 1) / sp) * 64;
+        sp = (P.K + kchunk - 1) / kchunk;
       }
       if (sp > 1 && used + mn * sp > part_cap) {
         launch_range(begin, i, flops, bytes);
@@ -1378,8 +1380,22 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 
 enum Op { OP_FWD, OP_REV, OP_SENS };
 
-size_t need_bytes(const int *n, int batch, int nb) {
-  size_t b = 2 * kPartBytes + recursion_bytes(nb) + 2 * kAlign;
+// Split-K partial region of one stream: 64 MB, or for the split-BF16 path
+// enough for its longest products (nb x n outputs, K up to n, FP32
+// accumulation over at most kMixMaxChunk of K) so that no split is capped.
+size_t part_bytes(int nmax, int nb, bool mixed) {
+  size_t b = kPartBytes;
+  if (mixed) {
+    const size_t need = sizeof(double) * (size_t)nb * nmax * (size_t)((nmax + kMixMaxChunk - 1) / kMixMaxChunk);
+    b = std::max(b, need);
+  }
+  return align_up(b);
+}
+
+size_t need_bytes(const int *n, int batch, int nb, bool mixed = false) {
+  int nmax = 0;
+  for (int i = 0; i < batch; ++i) nmax = std::max(nmax, n[i]);
+  size_t b = 2 * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 2 * kAlign;
   for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb) + 2 * kAlign;
   return b;
 }
@@ -1431,7 +1447,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   }
   if (nmax == 0) return CD_OK;
   const int nb = pick_nb(nmax, &opt, op == OP_FWD);
-  size_t need = need_bytes(n, batch, nb);
+  size_t need = need_bytes(n, batch, nb, opt.prec != CD_FP64);
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b) need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS);
   int rc = ensure_ws(h, need, s);
@@ -1441,11 +1457,12 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   ar.base = (char *)h->ws;
   ar.cap = h->ws_bytes;
   Ctx c{h, s, &opt, nullptr, 0, h->gemm_slots};
-  c.part = (double *)ar.take(kPartBytes);
-  c.part_cap = kPartBytes / sizeof(double);
+  const size_t pb = part_bytes(nmax, nb, opt.prec != CD_FP64);
+  c.part = (double *)ar.take(pb);
+  c.part_cap = pb / sizeof(double);
   c.side = h->side;
-  c.part2 = (double *)ar.take(kPartBytes);
-  c.part2_cap = kPartBytes / sizeof(double);
+  c.part2 = (double *)ar.take(pb);
+  c.part2_cap = pb / sizeof(double);
   std::vector<Prob> P;
   P.reserve(batch);
   for (int b = 0; b < batch; ++b) {
@@ -1608,7 +1625,7 @@ int cd_destroy(cd_handle *h) {
 int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes) {
   if (!h || !bytes || n_max < 0) return CD_EINVAL;
   const int nb = pick_nb(n_max, opt);
-  *bytes = need_bytes(&n_max, 1, nb) +
+  *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64) +
            ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0);
   return CD_OK;
 }

@@ -9,7 +9,8 @@
 //
 // One CTA computes a 128 x 128 output tile over its K range:
 //   warp 0, lane 0   issues the TMA loads of all terms of A and B per 64-wide K block;
-//   warp 1, lane 0   issues tcgen05.mma for every term product of the block;
+//   warp 1, lane 0   issues tcgen05.mma for every term product of the block
+//                    (leading product and corrections in two accumulators);
 //   warps 0-3        drain the FP32 accumulator from tensor memory (tcgen05.ld),
 //                    stage it in shared memory as FP64, and write
 //                    beta * Cin + alpha * acc (or a split-K partial) with
@@ -226,9 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
     s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == 1) {  // two accumulators: the leading term product, and the correction products
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -253,8 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
       tma_load_3d(sb, &d.tb, d.bx + kx, d.by + n0, 0, &full_bar[s]);
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: every kept term product of every 16-wide K step.
-    int issued = 0;
+    // MMA issuer: every kept term product of every 16-wide K step.  The
+    // leading product t0 t0 accumulates alone at columns [0, BN); the smaller
+    // corrections at [BN, 2 BN), so they never round against the large sum.
+    int issued_main = 0, issued_corr = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % S;
       if (!mbar_wait(&full_bar[s], (uint32_t)(kb / S) & 1u)) {
@@ -268,10 +271,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
       for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
         for (int q = 0; q < Terms<T>::n; ++q) {
-          const uint64_t ad = sw128_desc(sa + Terms<T>::a(q) * kTileBytes + kk * 32);
-          const uint64_t bd = sw128_desc(sb + Terms<T>::b(q) * kTileBytes + kk * 32);
-          mma_bf16(tmem, ad, bd, issued ? 1u : 0u);
-          issued = 1;
+          const int ta = Terms<T>::a(q), tb = Terms<T>::b(q);
+          const uint64_t ad = sw128_desc(sa + ta * kTileBytes + kk * 32);
+          const uint64_t bd = sw128_desc(sb + tb * kTileBytes + kk * 32);
+          if (ta == 0 && tb == 0) {
+            mma_bf16(tmem, ad, bd, issued_main ? 1u : 0u);
+            issued_main = 1;
+          } else {
+            mma_bf16(tmem + BN, ad, bd, issued_corr ? 1u : 0u);
+            issued_corr = 1;
+          }
         }
       }
       mma_commit(&empty_bar[s]);
@@ -291,17 +300,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
     const int row = warp * 32 + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
+      uint32_t r[32], q[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + c0), q);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) stage[row * LDS + c0 + i] = nkb > 0 ? (double)__uint_as_float(r[i]) : 0.0;
+      for (int i = 0; i < 32; ++i)
+        stage[row * LDS + c0 + i] =
+            nkb > 0 ? (double)__uint_as_float(r[i]) + (double)__uint_as_float(q[i]) : 0.0;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
   }
   if (err) {
     if (threadIdx.x == 0 && g.err) atomicExch(g.err, CD_ETIMEOUT);
