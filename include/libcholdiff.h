@@ -234,6 +234,17 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
  */
 int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority);
 
+/*
+ * Test hook for the device-side failure path (no counterpart in the paper).
+ * Runs one small tensor-core product whose first load barrier expects 16
+ * bytes more than its copy delivers: the copy completes, nothing else is in
+ * flight, and the consumer's bounded wait gives up after about 2 s.  The
+ * kernel then sets the handle's device error word to CD_ETIMEOUT, frees its
+ * tensor memory and exits without writing its output; the context stays
+ * usable.  Read the word with cd_get_last_device_error.
+ */
+int cd_debug_wait_timeout(cd_handle *h, void *stream);
+
 /* Read and clear the handle's device error word (synchronises the handle's
  * device).  *code receives CD_OK or a negative CD_* code. */
 int cd_get_last_device_error(cd_handle *h, int *code);

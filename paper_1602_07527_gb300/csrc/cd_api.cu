@@ -1731,6 +1731,39 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
   return c.err;
 }
 
+int cd_debug_wait_timeout(cd_handle *h, void *stream) {
+  if (!h) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  if (!mixed_available()) return CD_EINVAL;
+  const int T = 2, K = 64, M = 64;
+  const size_t bytes = 2 * (size_t)T * 2 * M * K + sizeof(double) * M * M + 4 * kAlign;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_ws(h, bytes, s);
+  if (rc) return rc;
+  Arena ar;
+  ar.base = (char *)h->ws;
+  ar.cap = h->ws_bytes;
+  void *As = ar.take(2 * (size_t)T * M * K);
+  double *C = (double *)ar.take(sizeof(double) * M * M);
+  if (!As || !C) return CD_ENOMEM;
+  if (cudaMemsetAsync(As, 0, 2 * (size_t)T * M * K, s) != cudaSuccess) return CD_ECUDA;
+  MProblem P;
+  memset(&P, 0, sizeof(P));
+  P.A = mop(As, K, M, T, 0, 0);
+  P.B = P.A;
+  P.M = P.N = M;
+  P.K = K;
+  P.Cout = C;
+  P.ldcout = M;
+  P.alpha = 1.0;
+  P.splits = 1;
+  P.kchunk = K;
+  int l = 0;
+  const cudaError_t e = mixed_gemm_launch(&P, 1, T, false, h->dev_err, s, &l, 16);
+  h->launches += l;
+  return e == cudaSuccess ? CD_OK : CD_ECUDA;
+}
+
 int cd_get_last_device_error(cd_handle *h, int *code) {
   if (!h || !code) return CD_EINVAL;
   DeviceGuard guard(h->device);

@@ -49,7 +49,8 @@ struct MDesc {  // 64-byte aligned through CUtensorMap
 };
 
 struct MGroup {
-  int count, total_tiles, lower, pad_;
+  int count, total_tiles, lower;
+  int tx_extra;  // test hook: bytes the first load barrier expects beyond the copy (0 in production)
   int *err;
   MDesc d[kMaxM];
 };
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
       }
       uint8_t *sa = smem + s * SB;
       uint8_t *sb = sa + T * kTileBytes;
-      mbar_expect_tx(&full_bar[s], SB);
+      mbar_expect_tx(&full_bar[s], SB + (kb == 0 ? (uint32_t)g.tx_extra : 0u));
       const int kx = kbeg + kb * BK;
       tma_load_3d(sa, &d.ta, d.ax + kx, d.ay + m0, 0, &full_bar[s]);
       tma_load_3d(sb, &d.tb, d.bx + kx, d.by + n0, 0, &full_bar[s]);
@@ -487,7 +488,7 @@ size_t mixed_workspace_bytes(int n, int nb, int prec) {
 }
 
 cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
-                              int *launches) {
+                              int *launches, int tx_extra) {
   if (T != 2 && T != 3) return cudaErrorInvalidValue;
   int i = 0;
   while (i < count) {
@@ -495,6 +496,7 @@ cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lowe
     memset(&g, 0, sizeof(g));
     g.lower = lower ? 1 : 0;
     g.err = dev_err;
+    g.tx_extra = tx_extra;
     bool any_split = false;
     long long biggest = 0;
     for (; i < count && g.count < kMaxM; ++i) {

@@ -47,8 +47,11 @@ int mixed_ctas_per_sm();                                // resident GEMM CTAs pe
 // Launch one grouped tensor-core GEMM (and its split-K reduction) over
 // `count` independent problems of the same term count and output mode.
 // dev_err: device word set to CD_ETIMEOUT if a bounded wait runs out.
+// tx_extra is a test hook (0 in production): the first load barrier of each
+// CTA expects that many bytes more than its copy delivers, so the bounded
+// wait of the MMA thread runs out and the kernel reports CD_ETIMEOUT.
 cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
-                              int *launches);
+                              int *launches, int tx_extra = 0);
 
 // Split an FP64 view into T BF16 term arrays (see MOp).  The view is
 // rows x cols of src (lower-triangle mode 1 keeps r >= c; mode 2 is the

@@ -82,6 +82,7 @@ def lib():
         L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
         L.cd_chol_rev_noalloc.argtypes = [_i, _vp, _ll, _vp, _ll, _i, _i, _vp]
         L.cd_set_priorities.argtypes = [_vp, _i, _i]
+        L.cd_debug_wait_timeout.argtypes = [_vp, _vp]
         L.cd_mixed_gemm_debug.argtypes = [_vp, _i, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _i, _i, _vp]
         _lib = L
     return _lib
@@ -93,7 +94,7 @@ def exported_symbols():
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
-            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities"]
+            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout"]
 
 
 def handle(device=None):
@@ -297,6 +298,18 @@ def launch_count(device=None, handle_=None):
 def device_error(device=None):
     code = _i()
     _check(lib().cd_get_last_device_error(handle(device), ctypes.byref(code)), "cd_get_last_device_error")
+    return code.value
+
+
+def debug_wait_timeout(device=None, handle_=None):
+    """Run the tensor-core kernel with a load barrier that never completes (test hook)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _check(lib().cd_debug_wait_timeout(_h(handle_, dev), _stream(dev)), "cd_debug_wait_timeout")
+
+
+def device_error_of(handle_):
+    code = _i()
+    _check(lib().cd_get_last_device_error(_vp(handle_.ptr), ctypes.byref(code)), "cd_get_last_device_error")
     return code.value
 
 
