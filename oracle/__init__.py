@@ -38,6 +38,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, ctypes.c_long]
             f.restype = ctypes.c_int
+        L.or_chol_unblocked_and_fwd.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, ctypes.c_long]
+        L.or_chol_unblocked_and_fwd.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
         L.or_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -102,6 +104,18 @@ def chol_unblocked_fwd(L, sigma_dot):
     n = _square(a, "sigma_dot")
     lib().or_chol_unblocked_fwd(n, _ptr(L), L.shape[1], _ptr(a), n)
     return np.tril(a)
+
+
+def chol_unblocked_and_fwd(sigma, sigma_dot):
+    """Sec. 4.1: chol_unblocked with the updates of chol_unblocked_fwd placed
+    in the same loop.  Returns (L, L_dot, info), info as chol_unblocked."""
+    a = _f64(sigma).copy()
+    ad = _f64(sigma_dot).copy()
+    n = _square(a, "sigma")
+    if ad.shape != a.shape:
+        raise ValueError("sigma_dot must match sigma")
+    info = lib().or_chol_unblocked_and_fwd(n, _ptr(a), n, _ptr(ad), n)
+    return np.tril(a), np.tril(ad), int(info)
 
 
 def chol_unblocked_rev(L, L_bar):

@@ -20,7 +20,9 @@
  * threads; it never changes the order of any sum.
  *
  * Pins (see tests/test_oracle_pins.py): LAPACK agreement and L L^T = Sigma for
- * or_chol_unblocked; the two forward-sensitivity routes against each other and
+ * or_chol_unblocked; the one-loop factorisation-and-sensitivity routine
+ * against finite differences of the factorisation and against the two
+ * routines run one after the other; the two forward-sensitivity routes against each other and
  * against central finite differences; the two reverse routes against each
  * other, against brute-force finite-difference Jacobians (N <= 6), against the
  * explicit element formula (Eq. delements), against the diagonal-Sigma closed
@@ -103,6 +105,47 @@ void or_chol_unblocked_fwd(int n, const double *L, long ldl, double *Ad, long ld
       AT(Ad, lda, i, j) = c / d;
     }
   }
+}
+
+/*
+ * chol_unblocked with its forward sensitivity accumulated in the same loop
+ * (Sec. 4.1: the updates of chol_unblocked_fwd may follow the matching
+ * updates of chol_unblocked).  For j = 0..n-1, column j of L is formed as in
+ * or_chol_unblocked, then column j of L_dot as in or_chol_unblocked_fwd; the
+ * latter reads only columns 0..j of L, all final by then.  tril(A) holds
+ * tril(Sigma) on entry and L on exit; tril(Ad) holds tril(Sigma_dot) on entry
+ * and L_dot on exit.  Returns 0 or, as or_chol_unblocked, the 1-based column
+ * of the first non-positive pivot (both outputs unspecified from there on).
+ */
+int or_chol_unblocked_and_fwd(int n, double *A, long lda, double *Ad, long ldad) {
+  for (int j = 0; j < n; ++j) {
+    /* column j of L */
+    double piv = AT(A, lda, j, j);
+    for (int k = 0; k < j; ++k) piv -= AT(A, lda, j, k) * AT(A, lda, j, k);
+    if (!(piv > 0.0)) return j + 1;
+    const double d = sqrt(piv);
+    AT(A, lda, j, j) = d;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < n; ++i) {
+      double ci = AT(A, lda, i, j);
+      for (int k = 0; k < j; ++k) ci -= AT(A, lda, i, k) * AT(A, lda, j, k); /* B r^T */
+      AT(A, lda, i, j) = ci / d;
+    }
+    /* column j of L_dot */
+    double dd = AT(Ad, ldad, j, j) / 2.0;
+    for (int k = 0; k < j; ++k) dd -= AT(A, lda, j, k) * AT(Ad, ldad, j, k);
+    dd = dd / d;
+    AT(Ad, ldad, j, j) = dd;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < n; ++i) {
+      double cdi = AT(Ad, ldad, i, j);
+      for (int k = 0; k < j; ++k) cdi -= AT(Ad, ldad, i, k) * AT(A, lda, j, k); /* B_dot r^T */
+      for (int k = 0; k < j; ++k) cdi -= AT(A, lda, i, k) * AT(Ad, ldad, j, k); /* B r_dot^T */
+      cdi -= AT(A, lda, i, j) * dd;                                             /* c d_dot   */
+      AT(Ad, ldad, i, j) = cdi / d;
+    }
+  }
+  return 0;
 }
 
 /*

@@ -26,6 +26,12 @@ MUTATIONS = [
     ("fwd_sens", "double dd = AT(Ad, lda, j, j) / 2.0;", "double dd = AT(Ad, lda, j, j);"),  # halving dropped
     ("fwd_sens", "c -= AT(L, ldl, i, k) * AT(Ad, lda, j, k); /* B r_dot^T */", ""),          # B r_dot^T dropped
     ("chol", "c -= AT(A, lda, i, k) * AT(A, lda, j, k);", "c -= AT(A, lda, i, k) * AT(A, lda, i, k);"),
+    ("fused", "cdi -= AT(A, lda, i, j) * dd;", ""),                                        # c d_dot dropped
+    ("fused", "double dd = AT(Ad, ldad, j, j) / 2.0;", "double dd = AT(Ad, ldad, j, j);"),  # halving dropped
+    ("fused", "ci -= AT(A, lda, i, k) * AT(A, lda, j, k); /* B r^T */",
+              "ci -= AT(A, lda, i, k) * AT(A, lda, i, k); /* B r^T */"),                     # index in L part
+    ("fused", "cdi -= AT(Ad, ldad, i, k) * AT(A, lda, j, k); /* B_dot r^T */",
+              "cdi += AT(Ad, ldad, i, k) * AT(A, lda, j, k); /* B_dot r^T */"),              # sign
     ("symrev", "for (int i = 0; i < n; ++i) X[(long)i * n + i] *= 2.0;", ""),                # P + P^T diagonal
     ("symrev", "phi_inplace(n, X);\n  /* M = P + P^T (full symmetric). */", "/* M = P + P^T (full symmetric). */"),
     ("symfwd", "for (int k = j; k <= i; ++k) s += AT(L, ldl, i, k) * X[(long)k * n + j];",
@@ -48,6 +54,8 @@ def _build_mutant(tmp_path, old, new):
         getattr(L, name).argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, ctypes.c_long]
     L.or_chol_unblocked.argtypes = [ctypes.c_int, dp, ctypes.c_long]
     L.or_chol_unblocked.restype = ctypes.c_int
+    L.or_chol_unblocked_and_fwd.argtypes = [ctypes.c_int, dp, ctypes.c_long, dp, ctypes.c_long]
+    L.or_chol_unblocked_and_fwd.restype = ctypes.c_int
     return L
 
 
@@ -73,7 +81,15 @@ def test_pins_catch_planted_mistake(oracle, tmp_path, routine, old, new):
     Lb = W.lbar(n, 21)
     Sd = W.sigma_dot(n, 21)
     mut = _build_mutant(tmp_path, old, new)
-    if routine == "chol":
+    if routine == "fused":
+        a = np.ascontiguousarray(S).copy()
+        ad = np.ascontiguousarray(Sd).copy()
+        dp = ctypes.POINTER(ctypes.c_double)
+        mut.or_chol_unblocked_and_fwd(n, a.ctypes.data_as(dp), n, ad.ctypes.data_as(dp), n)
+        ref = np.einsum("ijkl,kl->ij", J, np.tril(Sd))
+        assert (not np.allclose(np.tril(a), L, rtol=1e-10, atol=1e-12)
+                or oracle.rel_fro(np.tril(ad), ref) > 1e-6)
+    elif routine == "chol":
         got = _call(mut, "or_chol_unblocked", None, S)
         assert not np.allclose(got, L, rtol=1e-10, atol=1e-12)
     elif routine in ("rev", "symrev"):

@@ -91,6 +91,31 @@ def test_sens_central_fd(oracle, n):
     assert oracle.rel_fro(a, fd) <= 1e-8
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 40, 97])
+def test_one_loop_fwd_and_sens(oracle, n):
+    """Sec. 4.1's single loop: L against LAPACK, L_dot against central
+    differences of LAPACK's Cholesky (h = 1e-5), and both bit for bit against
+    the two routines run one after the other (same per-element arithmetic)."""
+    S = wishart(n)
+    Sd = W.sigma_dot(n, 1)
+    L, Ld, info = oracle.chol_unblocked_and_fwd(S, Sd)
+    assert info == 0
+    Lref = lapack_chol(S)
+    assert np.max(np.abs(L - Lref)) <= 1e-13 * np.max(np.abs(Lref))
+    h = 1e-5
+    fd = (lapack_chol(S + Sd * h / 2) - lapack_chol(S - Sd * h / 2)) / h
+    assert oracle.rel_fro(Ld, fd) <= 1e-8
+    L2, _ = oracle.chol_unblocked(S)
+    assert np.array_equal(L, L2)
+    assert np.array_equal(Ld, oracle.chol_unblocked_fwd(L2, Sd))
+
+
+def test_one_loop_fwd_and_sens_reports_info(oracle):
+    S = np.diag([4.0, 1.0, -1.0, 3.0])
+    _, _, info = oracle.chol_unblocked_and_fwd(S, np.eye(4))
+    assert info == 3
+
+
 def test_sens_n1_closed_form(oracle):
     L = np.array([[3.0]])
     out = oracle.chol_unblocked_fwd(L, np.array([[1.5]]))
