@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-dual", action="store_true", help="skip the one-loop chol_fwd_and_sens leg")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the served Poisson stream")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -311,6 +312,33 @@ def run_ours(args):
                "tflops": {"chol_fwd": flops_fwd, "chol_fwd_sens": flops_sens, "chol_rev": flops_rev}[k](n)
                / (statistics.median(v) * 1e-3) / 1e12} for k, v in op_ms.items()}
 
+    # the one-loop factorisation + forward sensitivity (Sec. 4.1-4.2) on the
+    # same inputs, against the two separate calls of the step above
+    def dual_step(prec="fp64"):
+        A.copy_(S0)
+        Ad.copy_(Sd0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        info = cd.chol_fwd_and_sens(A, Ad, nb=nb, prec=prec, diag=args.diag)
+        e[1].record(stream)
+        return e, info
+
+    def time_dual(prec="fp64"):
+        for _ in range(max(1, args.warmup - 1)):
+            dual_step(prec)
+        evs_d = [dual_step(prec) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if any(int(i.item()) != 0 for _, i in evs_d):
+            raise RuntimeError("factorisation reported a non-positive pivot")
+        return statistics.median(e[0].elapsed_time(e[1]) for e, _ in evs_d)
+
+    dual = None
+    if not args.no_dual:
+        dm = time_dual()
+        sep = ops["chol_fwd"]["ms_median"] + ops["chol_fwd_sens"]["ms_median"]
+        dual = {"ms_median": dm, "tflops": (flops_fwd(n) + flops_sens(n)) / (dm * 1e-3) / 1e12,
+                "separate_ms": sep, "speedup_vs_separate": sep / dm}
+
     # roofline of the dominant kernel (largest total device time in the timed region)
     dom = kstats[0] if kstats else None
     roofline = None
@@ -392,6 +420,10 @@ def run_ours(args):
             Ab.copy_(Lb0)
             cd.chol_rev(Lexact, Ab, nb=nb, prec=prec)
             e["Sigma_bar_given_fp64_L"] = rel(Ab, ref_Sb)
+            if not args.no_dual:
+                dms = time_dual(prec)
+                entry_dual = {"ms": dms, "separate_ms": mfwd + msens, "speedup_vs_separate": (mfwd + msens) / dms,
+                              "rel_err_vs_fp64": {"L": rel(A, ref_L), "L_dot": rel(Ad, ref_Ld)}}
             tk = next((k for k in mk if k["name"].startswith("mgemm")), None)
             entry = {"chol_rev_tflops": d.ws * flops_rev(n) / (d.max(mrev) * 1e-3) / 1e12,
                      "chol_fwd_tflops": flops_fwd(n) / (mfwd * 1e-3) / 1e12,
@@ -407,6 +439,8 @@ def run_ours(args):
                                             "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                                             "frac": ach / BF16_PEAK_TFLOPS,
                                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"}
+            if not args.no_dual:
+                entry["fwd_and_sens"] = entry_dual
             mixed[prec] = entry
 
     serving = None
@@ -425,7 +459,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: SE covariance (ell 0.3, points U[0,1]^3, jitter 1e-4), L_bar and Sigma_dot iid N(0,1)",
         "config": ours_config(args), "ops": ops, "roofline": roofline, "kernels": kernels,
-        "mixed": mixed, "serving": serving,
+        "fwd_and_sens": dual, "mixed": mixed, "serving": serving,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
         "step_tflops": d.ws * (flops_fwd(n) + flops_sens(n) + flops_rev(n)) / (total_ms / args.steps * 1e-3) / 1e12,
     }

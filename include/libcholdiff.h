@@ -7,6 +7,7 @@
  *   cd_chol_fwd       Sec. 4.2 chol_blocked      (LAPACK DPOTRF):  Sigma -> L
  *   cd_chol_fwd_sens  Sec. 4.2 chol_blocked_fwd  (forward mode):   (L, Sigma_dot) -> L_dot
  *   cd_chol_rev       Sec. 4.2 chol_blocked_rev  (reverse mode):   (L, L_bar) -> tril(Sigma_bar)
+ *   cd_chol_fwd_and_sens  the first two in one loop (Sec. 4.1-4.2): (Sigma, Sigma_dot) -> (L, L_dot)
  * with the problem statement of Sec. 2 (forward mode L_dot(L, Sigma_dot),
  * reverse mode Sigma_bar(L, L_bar)) and the symbolic results of Sec. 3
  * (Eqs. symfwd, symrev, symrevtril) as their exact meaning.
@@ -157,6 +158,20 @@ int cd_chol_fwd_sens(cd_handle *h, int n, const double *L, long long ldl,
                      double *Adot, long long lda, const cd_options *opt, void *stream);
 
 /*
+ * Factorisation and forward mode in one pass (Sec. 4.1 and Sec. 4.2: the
+ * forward-mode updates may be accumulated in the same loop as the
+ * factorisation).  On entry tril(A) = tril(Sigma) (n x n, lda) and
+ * tril(Adot) = tril(Sigma_dot) (n x n, ldadot); on exit tril(A) = L as
+ * cd_chol_fwd and tril(Adot) = L_dot as cd_chol_fwd_sens would give from that
+ * L, Eq. symfwd.  A and Adot must not overlap.  info as for cd_chol_fwd; on a
+ * non-positive pivot both outputs are unspecified from that column on.
+ * Blocking, precision (split-BF16 products for CD_MIXED_*) and the diagonal
+ * routine follow options as for the two separate calls.
+ */
+int cd_chol_fwd_and_sens(cd_handle *h, int n, double *A, long long lda, double *Adot, long long ldadot,
+                         const cd_options *opt, void *stream, int *info);
+
+/*
  * Batched variants over `batch` independent problems of ragged sizes.
  * n, A/L/Abar/Adot pointers and leading dimensions are HOST arrays of length
  * `batch` (the pointers inside are device pointers); problem b has size
@@ -174,6 +189,9 @@ int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *con
 int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L,
                              const long long *ldl, double *const *Adot, const long long *lda,
                              const cd_options *opt, void *stream);
+int cd_chol_fwd_and_sens_batched(cd_handle *h, int batch, const int *n, double *const *A,
+                                 const long long *lda, double *const *Adot, const long long *ldadot,
+                                 const cd_options *opt, void *stream, int *info);
 
 /*
  * Reverse mode without any allocation (no counterpart in the paper: this is a

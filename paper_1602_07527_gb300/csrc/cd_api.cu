@@ -67,17 +67,18 @@ int pick_nb(int n, const cd_options *opt, bool factorisation = false) {
 
 int nblocks(int n, int nb) { return (n + nb - 1) / nb; }
 
-// Workspace one problem of size n needs at one recursion level.
-size_t prob_bytes(int n, int nb) {
+// Workspace one problem of size n needs at one recursion level (dual: the
+// one-loop factorisation-and-sensitivity pass, which keeps a second panel).
+size_t prob_bytes(int n, int nb, bool dual = false) {
   if (n <= 0) return 0;
-  return align_up(sizeof(double) * (size_t)nblocks(n, nb) * nb * nb) + align_up(sizeof(double) * (size_t)n * nb) +
-         2 * align_up(sizeof(double) * (size_t)nb * nb);
+  return align_up(sizeof(double) * (size_t)nblocks(n, nb) * nb * nb) +
+         (dual ? 2 : 1) * align_up(sizeof(double) * (size_t)n * nb) + 2 * align_up(sizeof(double) * (size_t)nb * nb);
 }
 
 // Extra workspace of the recursive diagonal step (nb > kTileMax).
 size_t recursion_bytes(int nb) {
   if (nb <= kTileMax) return 0;
-  return prob_bytes(nb, kTileMax) + align_up(sizeof(double) * (size_t)nb * nb) + 4 * kAlign;
+  return prob_bytes(nb, kTileMax, true) + align_up(sizeof(double) * (size_t)nb * nb) + 4 * kAlign;
 }
 
 struct Prob {
@@ -96,6 +97,9 @@ struct Prob {
     int pad, T;
   } mx;
   double *T1, *T2;  // nb x nb temporaries of the symbolic diagonal step
+  double *Xd;       // one-loop pass: tril(Sigma_dot) in, L_dot out (null otherwise)
+  long long ldxd;
+  double *W2;       // one-loop pass: the solved L_dot panel (n * nb, ld nb)
 };
 
 // Per-launch event records of cd_profile_enable.
@@ -437,6 +441,7 @@ void sens_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
 void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
+void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 
 // inv (t x t, ld ldinv, zero above the diagonal) = tril(D)^{-1}.
 // t <= kTileMax: one CTA; larger: split D = [D11 0; D21 D22] and use
@@ -538,7 +543,7 @@ void precompute_dinv(Ctx &c, std::vector<Prob> &P, int nb, bool rev_partition, A
 bool bind_workspace(std::vector<Prob> &P, int nb, Arena &ar) {
   for (auto &p : P) {
     p.dinv = nullptr;
-    p.W = nullptr;
+    p.W = p.W2 = nullptr;
     p.T1 = p.T2 = nullptr;
     if (p.n <= 0) continue;
     p.dinv = (double *)ar.take(sizeof(double) * (size_t)nblocks(p.n, nb) * nb * nb);
@@ -546,6 +551,10 @@ bool bind_workspace(std::vector<Prob> &P, int nb, Arena &ar) {
     p.T1 = (double *)ar.take(sizeof(double) * (size_t)nb * nb);
     p.T2 = (double *)ar.take(sizeof(double) * (size_t)nb * nb);
     if (!p.dinv || !p.W || !p.T1 || !p.T2) return false;
+    if (p.Xd) {
+      p.W2 = (double *)ar.take(sizeof(double) * (size_t)p.n * nb);
+      if (!p.W2) return false;
+    }
   }
   return true;
 }
@@ -827,6 +836,157 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   }
 }
 
+// ------------- chol_blocked with chol_blocked_fwd in the same loop ----------
+// Sec. 4.2 notes that the forward-mode updates can be accumulated while the
+// factorisation is computed.  Step s finishes block column [j, k) of L (in X)
+// and of L_dot (in Xd).  The bulk products f3 and g3 read only finished
+// columns and run on the side stream; the chain f1, g1, f2, g2 runs on the
+// high-priority stream; f4 and g4 then solve both panels with the one
+// inverse of the new diagonal block.  A diagonal block wider than one tile
+// is itself processed by this routine with tile-sized blocks.
+void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  auto blk = [&](const Prob &p, int s, int &j, int &k) {
+    j = s * nb;
+    k = std::min(p.n, j + nb);
+    return j < p.n;
+  };
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();
+    {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
+      GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j, *Cd = p.Xd + (long long)k * p.ldxd + j;
+        const double *R = p.X + (long long)j * p.ldx;
+        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, R, p.ldx, C, p.ldx, C, p.ldx, -1.0, 1.0);
+        gb.add(m, w, j, p.Xd + (long long)k * p.ldxd, p.ldxd, R, p.ldx, Cd, p.ldxd, Cd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g3, second term: C_dot <- C_dot - B R_dot^T   (side stream)
+      GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Cd = p.Xd + (long long)k * p.ldxd + j;
+        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.Xd + (long long)j * p.ldxd, p.ldxd, Cd, p.ldxd, Cd,
+               p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T)
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        const double *R = p.X + (long long)j * p.ldx, *Rd = p.Xd + (long long)j * p.ldxd;
+        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
+        gb.add(w, w, j, R, p.ldx, R, p.ldx, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        gb.add(w, w, j, Rd, p.ldxd, R, p.ldx, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *Dd = p.Xd + (long long)j * p.ldxd + j;
+        gb.add(w, w, j, p.X + (long long)j * p.ldx, p.ldx, p.Xd + (long long)j * p.ldxd, p.ldxd, Dd, p.ldxd, Dd,
+               p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // f2: D <- chol_unblocked(D) and its inverse (wide blocks: both diagonal steps by recursion)
+      TileBatch tb(c, T_POTF2);
+      TileBatch ti(c, T_TRTRI);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
+          if (k < p.n || diag_symbolic(c, p, nb)) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
+          sub[0].Xd = p.Xd + (long long)j * p.ldxd + j;
+          sub[0].ldxd = p.ldxd;
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_dual(c, sub, kTileMax, ar);
+          if (k < p.n) trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          ar.off = mark;
+        }
+      }
+      tb.flush();  // the factorisations first, then the inverses of their results
+      ti.flush();
+    }
+    {  // g2 as the products of Eq. symfwd (problems that use them)
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || k - j > kTileMax || !diag_symbolic(c, p, nb)) continue;
+        v.push_back({p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.dinv, p.T1,
+                     p.T2, k - j, nb});
+      }
+      if (!v.empty()) sens_diag_symbolic(c, v);
+    }
+    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
+      TileBatch tb(c, T_SENS);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || k - j > kTileMax || diag_symbolic(c, p, nb)) continue;
+        tb.add(tdesc(p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, nullptr, 0,
+                     k - j));
+      }
+    }
+    c.join();
+    {  // f4: W = C D^{-T}, the finished panel of L
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv, nb, nullptr, 0, p.W, nb, 1.0, 0.0);
+      }
+    }
+    {  // g4: W2 = (C_dot - W D_dot^T) D^{-T}, the finished panel of L_dot
+      GemmBatch ga(c, A_N, B_TL, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Cd = p.Xd + (long long)k * p.ldxd + j;
+        ga.add(m, w, w, p.W, nb, p.Xd + (long long)j * p.ldxd + j, p.ldxd, Cd, p.ldxd, Cd, p.ldxd, -1.0, 1.0);
+      }
+      ga.flush();
+      GemmBatch gb(c, A_N, B_T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        gb.add(m, w, w, p.Xd + (long long)k * p.ldxd + j, p.ldxd, p.dinv, nb, nullptr, 0, p.W2, nb, 1.0, 0.0);
+      }
+    }
+    {
+      CopyBatch cb(c);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+        cb.add(p.W2, nb, p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w);
+      }
+    }
+  }
+}
 
 // ============================================================================
 // Mixed precision: the large off-diagonal products on the tensor cores with
@@ -1378,7 +1538,199 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   }
 }
 
-enum Op { OP_FWD, OP_REV, OP_SENS };
+// chol_blocked with chol_blocked_fwd in the same loop (as run_dual), products
+// in split BF16: the finished columns of L are split into `big`, those of
+// L_dot into `big2`; D^{-1} is split once per step for both panel solves.
+void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  const int T = P.empty() ? 2 : P[0].mx.T;
+  int nmax = 0;
+  for (auto &p : P) nmax = std::max(nmax, p.n);
+  const int steps = nblocks(nmax, nb);
+  auto blk = [&](const Prob &p, int s, int &j, int &k) {
+    j = s * nb;
+    k = std::min(p.n, j + nb);
+    return j < p.n;
+  };
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    c.fork();
+    {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
+      MixedBatch mb(c, T, false, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j, *Cd = p.Xd + (long long)k * p.ldxd + j;
+        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), R, m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
+        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, k), R, m, w, j, Cd, p.ldxd, Cd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g3, second term: C_dot <- C_dot - B R_dot^T   (side stream)
+      MixedBatch mb(c, T, false, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Cd = p.Xd + (long long)k * p.ldxd + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldxd,
+               Cd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T)
+      MixedBatch mb(c, T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
+        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
+        mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), R, w, w, j, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
+      MixedBatch mb(c, T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *Dd = p.Xd + (long long)j * p.ldxd + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldxd,
+               Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // f2: D <- chol_unblocked(D) and its inverse, FP64 (wide blocks: both diagonal steps by recursion)
+      TileBatch tb(c, T_POTF2);
+      TileBatch ti(c, T_TRTRI);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        if (w <= kTileMax) {
+          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
+          if (k < p.n || diag_symbolic(c, p, nb)) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+        } else {
+          tb.flush();
+          size_t mark = ar.off;
+          std::vector<Prob> sub(1);
+          sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
+          sub[0].Xd = p.Xd + (long long)j * p.ldxd + j;
+          sub[0].ldxd = p.ldxd;
+          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+          run_dual(c, sub, kTileMax, ar);
+          if (k < p.n) trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          ar.off = mark;
+        }
+      }
+      tb.flush();  // the factorisations first, then the inverses of their results
+      ti.flush();
+    }
+    {  // g2 as the products of Eq. symfwd (FP64)
+      std::vector<DiagRev> v;
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || k - j > kTileMax || !diag_symbolic(c, p, nb)) continue;
+        v.push_back({p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.dinv, p.T1,
+                     p.T2, k - j, nb});
+      }
+      if (!v.empty()) sens_diag_symbolic(c, v);
+    }
+    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
+      TileBatch tb(c, T_SENS);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || k - j > kTileMax || diag_symbolic(c, p, nb)) continue;
+        tb.add(tdesc(p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, nullptr, 0,
+                     k - j));
+      }
+    }
+    c.join();
+    {  // f4: W = C D^{-T}   (C -> P1, D^{-1} -> P4, tril(D_dot) -> P3 for g4)
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k)) continue;
+          const int w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+          sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, w, w, 1, 0, p.mx.P3, nb, nb, 0, 0, nb, nb, 0, 0, T);
+        }
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+               0.0);
+      }
+    }
+    {  // W -> C; the finished block column of L joins the split operand
+      CopyBatch cb(c);
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j, w, j,
+               j, T);
+      }
+      cb.flush();  // the solved panel must be in place before it is split
+      sb.flush();
+    }
+    {  // g4a: C_dot <- C_dot - C D_dot^T
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Cd = p.Xd + (long long)k * p.ldxd + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, j, k), mop(p.mx.P3, nb, nb, T, 0, 0), m, w, w, Cd, p.ldxd, Cd,
+               p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g4b: W2 = C_dot D^{-T}
+      {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k)) continue;
+          const int w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        }
+      }
+      MixedBatch mb(c, T, false);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W2, nb, 1.0,
+               0.0);
+      }
+    }
+    {  // W2 -> C_dot; the finished block column of L_dot joins its split operand
+      CopyBatch cb(c);
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        cb.add(p.W2, nb, p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w);
+        sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
+               w, j, j, T);
+      }
+      cb.flush();
+      sb.flush();
+    }
+  }
+}
+
+enum Op { OP_FWD, OP_REV, OP_SENS, OP_DUAL };
 
 // Split-K partial region of one stream: 64 MB, or for the split-BF16 path
 // enough for its longest products (nb x n outputs, K up to n, FP32
@@ -1392,11 +1744,11 @@ size_t part_bytes(int nmax, int nb, bool mixed) {
   return align_up(b);
 }
 
-size_t need_bytes(const int *n, int batch, int nb, bool mixed = false) {
+size_t need_bytes(const int *n, int batch, int nb, bool mixed = false, bool dual = false) {
   int nmax = 0;
   for (int i = 0; i < batch; ++i) nmax = std::max(nmax, n[i]);
   size_t b = 2 * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 2 * kAlign;
-  for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb) + 2 * kAlign;
+  for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb, dual) + 2 * kAlign;
   return b;
 }
 
@@ -1422,8 +1774,10 @@ int ensure_ws(cd_handle *h, size_t bytes, cudaStream_t s) {
 }
 
 int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, const long long *ldl,
-        double *const *X, const long long *ldx, const cd_options *opt_in, void *stream, int *info) {
+        double *const *X, const long long *ldx, const cd_options *opt_in, void *stream, int *info,
+        double *const *Xd = nullptr, const long long *ldxd = nullptr) {
   if (!h || batch < 0 || (batch > 0 && (!n || !X || !ldx))) return CD_EINVAL;
+  if (op == OP_DUAL && batch > 0 && (!Xd || !ldxd)) return CD_EINVAL;
   cd_options opt;
   cd_options_default(&opt);
   if (opt_in) opt = *opt_in;
@@ -1434,22 +1788,28 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   for (int b = 0; b < batch; ++b) {
     if (n[b] < 0 || ldx[b] < std::max(1, n[b])) return CD_EINVAL;
     if (n[b] > 0 && !X[b]) return CD_EINVAL;
-    if (op != OP_FWD) {
+    if (op == OP_REV || op == OP_SENS) {
       if (!L || !ldl) return CD_EINVAL;
       if (n[b] > 0 && (!L[b] || ldl[b] < n[b])) return CD_EINVAL;
+    }
+    if (op == OP_DUAL) {
+      if (ldxd[b] < std::max(1, n[b])) return CD_EINVAL;
+      if (n[b] > 0 && (!Xd[b] || Xd[b] == X[b])) return CD_EINVAL;
     }
     nmax = std::max(nmax, n[b]);
   }
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (op == OP_FWD && info && batch > 0) {
+  const bool factor = op == OP_FWD || op == OP_DUAL;
+  if (factor && info && batch > 0) {
     if (cudaMemsetAsync(info, 0, sizeof(int) * batch, s) != cudaSuccess) return CD_ECUDA;
   }
   if (nmax == 0) return CD_OK;
-  const int nb = pick_nb(nmax, &opt, op == OP_FWD);
-  size_t need = need_bytes(n, batch, nb, opt.prec != CD_FP64);
+  const int nb = pick_nb(nmax, &opt, factor);
+  size_t need = need_bytes(n, batch, nb, opt.prec != CD_FP64, op == OP_DUAL);
   if (opt.prec != CD_FP64)
-    for (int b = 0; b < batch; ++b) need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS);
+    for (int b = 0; b < batch; ++b)
+      need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL);
   int rc = ensure_ws(h, need, s);
   if (rc) return rc;
 
@@ -1467,13 +1827,18 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   P.reserve(batch);
   for (int b = 0; b < batch; ++b) {
     if (n[b] == 0) continue;
-    Prob p{n[b], op == OP_FWD ? nullptr : L[b], op == OP_FWD ? 0 : ldl[b], X[b], ldx[b],
-           info ? info + b : nullptr, nullptr, nullptr, 0};
+    Prob p{n[b], factor ? nullptr : L[b], factor ? 0 : ldl[b], X[b], ldx[b], info ? info + b : nullptr,
+           nullptr, nullptr, 0};
+    if (op == OP_DUAL) {
+      p.Xd = Xd[b];
+      p.ldxd = ldxd[b];
+    }
     P.push_back(p);
   }
   if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
   const bool mixed = opt.prec != CD_FP64;
-  if (mixed && (!mixed_available() || !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS, ar))) return CD_ENOMEM;
+  if (mixed && (!mixed_available() || !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar)))
+    return CD_ENOMEM;
   // The step loops issue the diagonal chain on the high-priority stream (its
   // CTAs are scheduled first when SM slots free up) and the independent bulk
   // GEMM of each step on the side stream; both start after, and the caller's
@@ -1487,6 +1852,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     case OP_FWD: mixed ? run_fwd_mixed(c, P, nb, ar) : run_fwd(c, P, nb, ar); break;
     case OP_REV: mixed ? run_rev_mixed(c, P, nb, ar) : run_rev(c, P, nb, ar); break;
     case OP_SENS: mixed ? run_sens_mixed(c, P, nb, ar) : run_sens(c, P, nb, ar); break;
+    case OP_DUAL: mixed ? run_dual_mixed(c, P, nb, ar) : run_dual(c, P, nb, ar); break;
   }
   if (h->crit) {
     c.join();
@@ -1625,7 +1991,7 @@ int cd_destroy(cd_handle *h) {
 int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes) {
   if (!h || !bytes || n_max < 0) return CD_EINVAL;
   const int nb = pick_nb(n_max, opt);
-  *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64) +
+  *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64, true) +
            ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0);
   return CD_OK;
 }
@@ -1675,6 +2041,19 @@ int cd_chol_rev_batched(cd_handle *h, int batch, const int *n, const double *con
 int cd_chol_fwd_sens_batched(cd_handle *h, int batch, const int *n, const double *const *L, const long long *ldl,
                              double *const *Adot, const long long *lda, const cd_options *opt, void *stream) {
   return run(h, OP_SENS, batch, n, L, ldl, Adot, lda, opt, stream, nullptr);
+}
+
+int cd_chol_fwd_and_sens(cd_handle *h, int n, double *A, long long lda, double *Adot, long long ldadot,
+                         const cd_options *opt, void *stream, int *info) {
+  double *X[1] = {A}, *Xd[1] = {Adot};
+  long long ld[1] = {lda}, ldd[1] = {ldadot};
+  return run(h, OP_DUAL, 1, &n, nullptr, nullptr, X, ld, opt, stream, info, Xd, ldd);
+}
+
+int cd_chol_fwd_and_sens_batched(cd_handle *h, int batch, const int *n, double *const *A, const long long *lda,
+                                 double *const *Adot, const long long *ldadot, const cd_options *opt, void *stream,
+                                 int *info) {
+  return run(h, OP_DUAL, batch, n, nullptr, nullptr, A, lda, opt, stream, info, Adot, ldadot);
 }
 
 int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {

@@ -459,6 +459,7 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
     case T_REV: k_tile<T_REV><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_SENS: k_tile<T_SENS><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_TRTRI: return launch_trtri_group(g, s);
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

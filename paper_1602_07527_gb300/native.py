@@ -74,6 +74,8 @@ def lib():
         L.cd_chol_fwd_batched.argtypes = [_vp, _i, _vp, _vp, _vp, P(Options), _vp, _vp]
         L.cd_chol_rev_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp]
         L.cd_chol_fwd_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp]
+        L.cd_chol_fwd_and_sens.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp, _vp]
+        L.cd_chol_fwd_and_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp, _vp]
         L.cd_get_last_device_error.argtypes = [_vp, P(_i)]
         L.cd_launch_count.argtypes = [_vp]
         L.cd_launch_count.restype = _ll
@@ -94,7 +96,8 @@ def exported_symbols():
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
-            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout"]
+            "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout",
+            "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched"]
 
 
 def handle(device=None):
@@ -224,6 +227,23 @@ def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None, diag="auto"):
     return Adot
 
 
+def chol_fwd_and_sens(A, Adot, nb=0, prec="fp64", info=None, handle_=None, diag="auto"):
+    """In place, in one pass: tril(A) = tril(Sigma) -> L and
+    tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.1-4.2: the forward-mode
+    updates accumulated in the factorisation's loop).  Returns the info tensor."""
+    n, lda = _mat(A, "A")
+    n2, ldd = _mat(Adot, "Adot")
+    if n != n2 or A.device != Adot.device:
+        raise ValueError("A and Adot must have the same size and device")
+    dev = A.device
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+    o = options(nb, prec, diag=diag)
+    _check(lib().cd_chol_fwd_and_sens(_h(handle_, dev), n, _vp(A.data_ptr()), lda, _vp(Adot.data_ptr()), ldd,
+                                      ctypes.byref(o), _stream(dev), _vp(info.data_ptr())), "cd_chol_fwd_and_sens")
+    return info
+
+
 def _arrays(mats, name):
     ns, lds, ptrs = [], [], []
     for t in mats:
@@ -274,6 +294,22 @@ def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None, diag="auto
     _check(lib().cd_chol_fwd_sens_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_fwd_sens_batched")
     return Adots
+
+
+def chol_fwd_and_sens_batched(As, Adots, nb=0, prec="fp64", info=None, handle_=None, diag="auto"):
+    b, n, lda, pa, ns = _arrays(As, "A")
+    b2, n2, ldd, pd, ns2 = _arrays(Adots, "Adot")
+    if b != b2 or ns != ns2:
+        raise ValueError("A and Adot lists must match")
+    if b == 0:
+        return info
+    dev = As[0].device
+    if info is None:
+        info = torch.zeros(b, dtype=torch.int32, device=dev)
+    o = options(nb, prec, diag=diag)
+    _check(lib().cd_chol_fwd_and_sens_batched(_h(handle_, dev), b, n, pa, lda, pd, ldd, ctypes.byref(o),
+                                              _stream(dev), _vp(info.data_ptr())), "cd_chol_fwd_and_sens_batched")
+    return info
 
 
 def mixed_gemm_debug(A, B, C, prec="bf16x3", lower=False):
