@@ -37,15 +37,23 @@ constexpr uint32_t kTileBytes = BM * BK * 2;  // one term of one operand per K b
 constexpr unsigned long long kTimeoutNs = 2000000000ULL;
 constexpr int kMaxM = 10;
 
+// How an FP64 output is formed from the accumulated product a (chosen on
+// the host from alpha and beta, so that the common cases need no FP64
+// multiply: on this GPU every FP64 instruction occupies a narrow unit for
+// about 64 cycles per warp).
+enum Comb { kCopy = 0, kNeg = 1, kScale = 2, kAdd = 3, kSub = 4, kAxpy = 5, kGeneral = 6 };
+
 struct MDesc {  // 64-byte aligned through CUtensorMap
   CUtensorMap ta, tb;
   const double *Cin;
-  double *Cout, *part;
+  double *Cout;
+  float *part;  // split-K partial sums (FP32, as accumulated)
   long long ldcin, ldcout;
   double alpha, beta;
   int M, N, K, splits, kchunk;
   int tiles_m, tiles_n, tile_begin;
   int ax, ay, bx, by;
+  int comb;     // a Comb value
 };
 
 struct MGroup {
@@ -62,6 +70,69 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN 
                             ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// IEEE-754 conversions written with integer operations.  On this GPU the
+// conversion instructions between FP32 and FP64 run on the FP64 unit (about
+// 80 cycles per warp), while integer and FP32 instructions issue every few
+// cycles; these run once per element of every product and every split.
+
+// binary32 -> binary64, exact: rebias the exponent and widen the significand
+// (a subnormal input is normalised by its leading-one position).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint64_t sg = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  uint64_t r;
+  if (e - 1u < 254u) {
+    r = sg | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (e == 0xFFu) {
+    r = sg | 0x7FF0000000000000ull | ((uint64_t)m << 29);
+  } else if (m == 0) {
+    r = sg;
+  } else {  // m 2^-149 = 1.f 2^(p - 149), p the leading-one position of m
+    const int p = 31 - __clz((int)m);
+    r = sg | ((uint64_t)(p + 874) << 52) | ((uint64_t)(m ^ (1u << p)) << (52 - p));
+  }
+  return __longlong_as_double((long long)r);
+}
+
+// binary64 x -> (hi, lo) in binary32: hi is x with its significand cut to 24
+// bits (exact), lo the remaining 29 bits rounded to 24, so that
+// |x - hi - lo| <= 2^-47 |x|.  Outside FP32's normal range: below it both
+// parts are zero, above it hi is +-inf, NaN stays NaN.
+__device__ __forceinline__ void f64_to_f32x2(double x, float &hi, float &lo) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sg = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  const int fe = e - 896;  // binary32 biased exponent of x
+  lo = 0.0f;
+  if (fe >= 1 && fe <= 254) {
+    hi = __uint_as_float(sg | ((uint32_t)fe << 23) | (uint32_t)(m >> 29));
+    const uint32_t r = (uint32_t)(m & 0x1FFFFFFFu);  // remainder r 2^(e - 1075)
+    if (r != 0) {
+      const uint32_t rb = __float_as_uint(__uint2float_rn(r));
+      const int re = (int)(rb >> 23) + (e - 1075);  // rescale through the exponent field
+      if (re >= 1) lo = __uint_as_float(sg | ((uint32_t)re << 23) | (rb & 0x7FFFFFu));
+    }
+  } else if (e == 0x7FF) {
+    hi = __uint_as_float(sg | 0x7F800000u | (m ? 0x400000u : 0u));
+  } else {
+    hi = __uint_as_float(fe > 254 ? (sg | 0x7F800000u) : sg);
+  }
+}
+
+__device__ __forceinline__ double combine(int comb, double a, double cin, double alpha, double beta) {
+  switch (comb) {
+    case kCopy: return a;
+    case kNeg: return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+    case kScale: return alpha * a;
+    case kAdd: return cin + a;
+    case kSub: return cin - a;
+    case kAxpy: return fma(alpha, a, cin);
+    default: return fma(alpha, a, beta * cin);
+  }
+}
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -290,12 +361,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
   }
   __syncwarp();
 
-  // Epilogue: accumulator (FP32, tensor memory) -> FP64 staging -> global.
+  // Epilogue: accumulators (FP32, tensor memory) -> their FP32 sum, staged
+  // in shared memory -> FP64 output with one FP64 operation per element.
+  // The corrections were accumulated apart from the leading product; adding
+  // the two once here rounds once at 2^-24, far below the accumulation's own
+  // rounding over K.
   if (!mbar_wait(&done_bar, 0)) s_err = 1;
   tc_fence_after();
   __syncthreads();
   const bool err = s_err != 0;
-  double *stage = (double *)smem;
+  float *stage = (float *)smem;
   constexpr int LDS = BN + 1;
   if (!err) {
     const int row = warp * 32 + lane;
@@ -306,8 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + c0), q);
 #pragma unroll
       for (int i = 0; i < 32; ++i)
-        stage[row * LDS + c0 + i] =
-            nkb > 0 ? (double)__uint_as_float(r[i]) + (double)__uint_as_float(q[i]) : 0.0;
+        stage[row * LDS + c0 + i] = nkb > 0 ? __uint_as_float(r[i]) + __uint_as_float(q[i]) : 0.0f;
     }
   }
   tc_fence_before();
@@ -325,9 +399,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
   // thread only ever rewrites the elements it has read), so the loads of a
   // chunk are in flight together instead of one global round trip per row.
   const int j = n0 + threadIdx.x;
-  const double alpha = d.alpha, beta = d.beta;
   const bool col_ok = j < d.N;
   const int rows = min(BM, d.M - m0);
+  if (d.splits > 1) {  // FP32 partial sums; the reduction forms the FP64 output
+    if (col_ok)
+      for (int r = 0; r < rows; ++r) {
+        const int i = m0 + r;
+        if (!(LOWER && j > i)) d.part[((long long)z * d.M + i) * d.N + j] = stage[r * LDS + threadIdx.x];
+      }
+    return;
+  }
+  const int comb = d.comb;
+  const double alpha = d.alpha, beta = d.beta;
+  const bool use_cin = comb >= kAdd;
   constexpr int CH = 16;
   for (int r0 = 0; r0 < rows; r0 += CH) {
     double cin[CH];
@@ -335,42 +419,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
     for (int q = 0; q < CH; ++q) {
       const int r = r0 + q, i = m0 + r;
       cin[q] = 0.0;
-      if (d.splits == 1 && beta != 0.0 && col_ok && r < rows && !(LOWER && j > i))
-        cin[q] = d.Cin[(long long)i * d.ldcin + j];
+      if (use_cin && col_ok && r < rows && !(LOWER && j > i)) cin[q] = d.Cin[(long long)i * d.ldcin + j];
     }
 #pragma unroll
     for (int q = 0; q < CH; ++q) {
       const int r = r0 + q, i = m0 + r;
       if (!col_ok || r >= rows || (LOWER && j > i)) continue;
-      double v = alpha * stage[r * LDS + threadIdx.x];
-      if (d.splits == 1) {
-        if (beta != 0.0) v = fma(beta, cin[q], v);
-        d.Cout[(long long)i * d.ldcout + j] = v;
-      } else {
-        d.part[((long long)z * d.M + i) * d.N + j] = v;
-      }
+      d.Cout[(long long)i * d.ldcout + j] = combine(comb, f32_to_f64(stage[r * LDS + threadIdx.x]), cin[q], alpha, beta);
     }
   }
 }
 
-// Split-K reduction in FP64, partials summed in order.
+// Split-K reduction: the FP32 partials, in order, by compensated summation
+// in FP32 (Neumaier's variant of Kahan summation: the rounding error of each
+// addition, obtained exactly, is carried in c), then s + c to FP64 and the
+// output formed as in the product's epilogue.
 template <bool LOWER>
 __global__ void k_mreduce(const __grid_constant__ MGroup g) {
   const MDesc &d = g.d[blockIdx.y];
   if (d.splits <= 1) return;
   const long long total = (long long)d.M * d.N;
+  const int comb = d.comb;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / d.N), j = (int)(e - (long long)i * d.N);
     if (LOWER && j > i) continue;
-    double s = 0.0;
-    for (int z = 0; z < d.splits; ++z) s += d.part[(long long)z * total + e];
-    if (d.beta != 0.0) s = fma(d.beta, d.Cin[(long long)i * d.ldcin + j], s);
-    d.Cout[(long long)i * d.ldcout + j] = s;
+    float s = 0.0f, c = 0.0f;
+    for (int z = 0; z < d.splits; ++z) {
+      const float x = d.part[(long long)z * total + e];
+      const float t = s + x;
+      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    const double a = f32_to_f64(s) + f32_to_f64(c);
+    const double cin = comb >= kAdd ? d.Cin[(long long)i * d.ldcin + j] : 0.0;
+    d.Cout[(long long)i * d.ldcout + j] = combine(comb, a, cin, d.alpha, d.beta);
   }
 }
 
-// FP64 -> T BF16 terms, each rounded from the exact remainder of the previous ones.
+// FP64 -> T BF16 terms.  x is first cut exactly into FP32 pieces hi + lo
+// (integer operations, no FP64 instruction); t0 is the BF16 nearest to hi,
+// and each further term the BF16 nearest to the remainder so far,
+// (hi - t0 - ...) + lo, formed in FP32: hi - t0 is exact, and adding lo
+// rounds at 2^-24 of the remainder, far below the last term kept.
 __device__ void split_body(const SplitArgs &a, long long first, long long stride) {
   __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
   const long long tstride = a.dst_rows * a.ldd;
@@ -380,28 +471,26 @@ __device__ void split_body(const SplitArgs &a, long long first, long long stride
   for (long long e = first; e < total; e += stride) {
     const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
     const int vr = a.reg_r0 + rr - a.dst_r0, vc = a.reg_c0 + cc - a.dst_c0;
-    double x = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     if (vr >= 0 && vc >= 0 && vr < vr_n && vc < vc_n) {
       const int r = a.transpose ? vc : vr, c = a.transpose ? vr : vc;
-      if (a.mode == 0) {
-        x = a.src[(long long)r * a.lds + c];
-      } else if (a.mode == 1) {
-        x = r >= c ? a.src[(long long)r * a.lds + c] : 0.0;
-      } else {
-        x = r > c ? a.src[(long long)r * a.lds + c]
-                  : (r < c ? a.src[(long long)c * a.lds + r] : 2.0 * a.src[(long long)r * a.lds + r]);
+      const bool upper = r < c;
+      if (a.mode == 0 || !upper || a.mode == 2) {
+        const long long off = upper && a.mode == 2 ? (long long)c * a.lds + r : (long long)r * a.lds + c;
+        f64_to_f32x2(a.src[off], hi, lo);
+        if (a.mode == 2 && r == c) {  // doubled diagonal: exact in FP32
+          hi *= 2.0f;
+          lo *= 2.0f;
+        }
       }
     }
     const long long o = (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc;
-    const __nv_bfloat16 t0 = __float2bfloat16_rn((float)x);
-    const double r1 = x - (double)__bfloat162float(t0);
-    const __nv_bfloat16 t1 = __float2bfloat16_rn((float)r1);
+    const __nv_bfloat16 t0 = __float2bfloat16_rn(hi);
+    const float d0 = hi - __bfloat162float(t0);
+    const __nv_bfloat16 t1 = __float2bfloat16_rn(d0 + lo);
     dst[o] = t0;
     dst[tstride + o] = t1;
-    if (a.T == 3) {
-      const double r2 = r1 - (double)__bfloat162float(t1);
-      dst[2 * tstride + o] = __float2bfloat16_rn((float)r2);
-    }
+    if (a.T == 3) dst[2 * tstride + o] = __float2bfloat16_rn((d0 - __bfloat162float(t1)) + lo);
   }
 }
 
@@ -509,7 +598,10 @@ cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lowe
       if (!encode_map(&d.ta, P.A) || !encode_map(&d.tb, P.B)) return cudaErrorInvalidValue;
       d.Cin = P.Cin;
       d.Cout = P.Cout;
-      d.part = P.part;
+      d.part = reinterpret_cast<float *>(P.part);  // the region holds splits * M * N doubles: ample for floats
+      d.comb = P.beta == 0.0 ? (P.alpha == 1.0 ? kCopy : P.alpha == -1.0 ? kNeg : kScale)
+               : P.beta == 1.0 ? (P.alpha == 1.0 ? kAdd : P.alpha == -1.0 ? kSub : kAxpy)
+                               : kGeneral;
       d.ldcin = P.ldcin;
       d.ldcout = P.ldcout;
       d.alpha = P.alpha;

@@ -1,11 +1,13 @@
 // Mixed-precision (split-BF16, tcgen05) engine interface.
 //
 // FP64 operands are split into T = 2 or 3 BF16 terms, x ~ t0 + t1 (+ t2), each
-// term rounded to nearest from the exact FP64 remainder of the previous ones.
-// A product is formed as the sum of the term products whose order is at most
-// 2^-8 (T = 2: t0 t0, t0 t1, t1 t0) or 2^-16 (T = 3: adds t0 t2, t2 t0, t1 t1)
-// relative to the leading one, accumulated in FP32 in tensor memory, and added
-// to the FP64 output in FP64.
+// term the BF16 nearest to the remainder of the previous ones (formed in FP32
+// from an exact two-piece FP32 form of x, so within 2^-24 of the exact
+// remainder).  A product is formed as the sum of the term products whose
+// order is at most 2^-8 (T = 2: t0 t0, t0 t1, t1 t0) or 2^-16 (T = 3: adds
+// t0 t2, t2 t0, t1 t1) relative to the leading one, accumulated in FP32 in
+// tensor memory (the leading product apart from the corrections), and added
+// to the FP64 output in FP64.  Split-K partial sums are FP32.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
