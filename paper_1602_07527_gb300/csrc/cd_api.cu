@@ -1060,7 +1060,9 @@ struct MixedBatch {
   static constexpr int kCap = 40;
   MProblem v[kCap];
   int count = 0;
-  MixedBatch(Ctx &ctx, int T_, bool lower_, bool on_side = false) : c(ctx), T(T_), lower(lower_) {
+  const char *tag;  // the algorithm step, for the profile
+  MixedBatch(Ctx &ctx, int T_, bool lower_, bool on_side = false, const char *tag_ = nullptr)
+      : c(ctx), T(T_), lower(lower_), tag(tag_) {
     const bool side = on_side && c.side;
     st = side ? c.side : c.s;
     part = side ? c.part2 : c.part;
@@ -1098,7 +1100,7 @@ struct MixedBatch {
     if (e <= b) return;
     const int prods = T == 3 ? 6 : 3;
     char name[48];
-    snprintf(name, sizeof(name), "mgemm_bf16x%d%s", prods, lower ? "_tril" : "");
+    snprintf(name, sizeof(name), "mgemm_bf16x%d%s%s%s", prods, lower ? "_tril" : "", tag ? " " : "", tag ? tag : "");
     c.launch(name, flops, bytes, st, [&] {
       int l = 0;
       cudaError_t err = mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l);
@@ -1210,7 +1212,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 1, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "r1");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1234,7 +1236,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     c.fork();
     {  // r2 (side stream): B_bar <- B_bar - C_bar R
-      MixedBatch mb(c, T, false, /*on_side=*/true);
+      MixedBatch mb(c, T, false, true, "r2");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1245,7 +1247,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // r3: D_bar <- tril(D_bar) - tril(C_bar^T C)
-      MixedBatch mb(c, T, true);
+      MixedBatch mb(c, T, true, false, "r3");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1297,7 +1299,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                 (int)p.mx.ldn, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "r5");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k) || j == 0) continue;
@@ -1321,7 +1323,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
     {  // f3 (side stream): C <- C - B R^T
-      MixedBatch mb(c, T, false, true);
+      MixedBatch mb(c, T, false, true, "f3");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1332,7 +1334,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f1: D <- D - tril(R R^T)
-      MixedBatch mb(c, T, true);
+      MixedBatch mb(c, T, true, false, "f1");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1380,7 +1382,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "f4");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1423,7 +1425,7 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
     for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T
-      MixedBatch mb(c, T, false, true);
+      MixedBatch mb(c, T, false, true, "g3");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1435,7 +1437,7 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
-      MixedBatch mb(c, T, true);
+      MixedBatch mb(c, T, true, false, "g1");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1490,7 +1492,7 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "g4a");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1512,7 +1514,7 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "g4b");
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -1554,7 +1556,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
     {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
-      MixedBatch mb(c, T, false, true);
+      MixedBatch mb(c, T, false, true, "f3+g3");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1566,7 +1568,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // g3, second term: C_dot <- C_dot - B R_dot^T   (side stream)
-      MixedBatch mb(c, T, false, true);
+      MixedBatch mb(c, T, false, true, "g3");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1577,7 +1579,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T)
-      MixedBatch mb(c, T, true);
+      MixedBatch mb(c, T, true, false, "f1+g1");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1589,7 +1591,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
-      MixedBatch mb(c, T, true);
+      MixedBatch mb(c, T, true, false, "g1");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1659,7 +1661,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, w, w, 1, 0, p.mx.P3, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "f4");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1683,7 +1685,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       sb.flush();
     }
     {  // g4a: C_dot <- C_dot - C D_dot^T
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "g4a");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1704,7 +1706,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false);
+      MixedBatch mb(c, T, false, false, "g4b");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;

@@ -32,7 +32,8 @@ namespace cd {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 8;                  // epilogue warps: two per tensor-memory lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr uint32_t kTileBytes = BM * BK * 2;  // one term of one operand per K block (BM == BN)
 constexpr unsigned long long kTimeoutNs = 2000000000ULL;
 constexpr int kMaxM = 10;
@@ -122,15 +123,51 @@ __device__ __forceinline__ void f64_to_f32x2(double x, float &hi, float &lo) {
   }
 }
 
-__device__ __forceinline__ double combine(int comb, double a, double cin, double alpha, double beta) {
+// The output from the accumulated product a, for one Comb mode.  The mode is
+// a template argument so that each row loop holds exactly its own arithmetic:
+// with a runtime switch the compiler evaluates every case under predicates,
+// and each predicated-off FP64 instruction still holds the FP64 unit.
+template <int COMB>
+__device__ __forceinline__ double combine(double a, double cin, double alpha, double beta) {
+  if (COMB == kCopy) return a;
+  if (COMB == kNeg) return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+  if (COMB == kScale) return alpha * a;
+  if (COMB == kAdd) return cin + a;
+  if (COMB == kSub) return cin - a;
+  if (COMB == kAxpy) return fma(alpha, a, cin);
+  return fma(alpha, a, beta * cin);
+}
+
+// Writes rows [0, nrows) of one output column j (rows rbase + rr) from the
+// FP32 staging column stw[rr * ld], forming each value under mode COMB.
+template <int COMB, bool LOWER>
+__device__ __forceinline__ void write_column(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j) {
+  constexpr bool kUseCin = COMB >= kAdd;
+  double cin[32];
+#pragma unroll
+  for (int rr = 0; rr < 32; ++rr) {
+    const int i = rbase + rr;
+    cin[rr] = (kUseCin && rr < nrows && !(LOWER && j > i)) ? d.Cin[(long long)i * d.ldcin + j] : 0.0;
+  }
+#pragma unroll
+  for (int rr = 0; rr < 32; ++rr) {
+    const int i = rbase + rr;
+    if (rr < nrows && !(LOWER && j > i))
+      d.Cout[(long long)i * d.ldcout + j] = combine<COMB>(f32_to_f64(stw[rr * ld]), cin[rr], d.alpha, d.beta);
+  }
+}
+
+template <bool LOWER>
+__device__ __forceinline__ void write_column_any(int comb, const MDesc &d, const float *stw, int ld, int rbase,
+                                                 int nrows, int j) {
   switch (comb) {
-    case kCopy: return a;
-    case kNeg: return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
-    case kScale: return alpha * a;
-    case kAdd: return cin + a;
-    case kSub: return cin - a;
-    case kAxpy: return fma(alpha, a, cin);
-    default: return fma(alpha, a, beta * cin);
+    case kCopy: write_column<kCopy, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kNeg: write_column<kNeg, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kScale: write_column<kScale, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kAdd: write_column<kAdd, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kSub: write_column<kSub, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kAxpy: write_column<kAxpy, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    default: write_column<kGeneral, LOWER>(d, stw, ld, rbase, nrows, j); break;
   }
 }
 
@@ -247,61 +284,109 @@ template <int T>
 __host__ __device__ constexpr uint32_t stage_bytes() {
   return 2u * T * kTileBytes;
 }
+// Epilogue staging: one 32 x 32 FP32 block per epilogue warp (padded rows).
+constexpr int kEpiLd = 33;
+constexpr size_t kEpiBytes = (size_t)kEpiWarps * 32 * kEpiLd * sizeof(float);
 template <int T>
 constexpr size_t dyn_smem() {
-  return (size_t)stages<T>() * stage_bytes<T>() + 1024;
+  return (size_t)stages<T>() * stage_bytes<T>() + kEpiBytes + 1024;
 }
-static_assert((size_t)BM * (BN + 1) * sizeof(double) <= (size_t)stages<2>() * stage_bytes<2>(), "staging");
-static_assert((size_t)BM * (BN + 1) * sizeof(double) <= (size_t)stages<3>() * stage_bytes<3>(), "staging");
+static_assert(dyn_smem<2>() <= 232448 && dyn_smem<3>() <= 232448, "shared memory per CTA");
 
+// One output tile of one problem: the work of a CTA for a while.
+struct Unit {
+  int p, z, m0, n0, kbeg, nkb;
+};
+
+template <bool LOWER>
+__device__ __forceinline__ Unit decode_unit(const MGroup &g, int u) {
+  Unit x;
+  int p = 0;
+  while (p + 1 < g.count && u >= g.d[p + 1].tile_begin) ++p;
+  const MDesc &d = g.d[p];
+  const int local = u - d.tile_begin;
+  const int per_split = LOWER ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
+  x.p = p;
+  x.z = local / per_split;
+  const int rem = local - x.z * per_split;
+  if (LOWER) {
+    int ti = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
+    while (ti * (ti + 1) / 2 > rem) --ti;
+    x.m0 = ti * BM;
+    x.n0 = (rem - ti * (ti + 1) / 2) * BN;
+  } else {
+    x.m0 = (rem / d.tiles_n) * BM;
+    x.n0 = (rem % d.tiles_n) * BN;
+  }
+  x.kbeg = x.z * d.kchunk;
+  const int kend = min(d.K, x.kbeg + d.kchunk);
+  x.nkb = kend > x.kbeg ? (kend - x.kbeg + BK - 1) / BK : 0;
+  return x;
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has
+// recorded a failure in *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort || globaltimer() - t0 > kTimeoutNs) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent, warp-specialised product.  A CTA takes the units
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the group:
+//   warp 0        lane 0 streams every unit's K blocks through the stage ring
+//                 with TMA; the whole warp first pulls the unit's Cin rows
+//                 into L2 for the epilogue;
+//   warp 1        lane 0 issues the tcgen05.mma of each unit into one of two
+//                 tensor-memory accumulator sets (256 columns each: leading
+//                 product and corrections), alternating between units;
+//   warps 2-9     drain a finished accumulator set (each warp 32 tensor
+//                 memory lanes, i.e. rows, and half of the columns, 32 at a
+//                 time through shared memory) and write the FP64 output or
+//                 FP32 split-K partials, while the MMA warp already fills the
+//                 other set.  Two warps per sub-partition hide each other's
+//                 load and store latency.
 template <int T, bool LOWER>
 __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ MGroup g) {
   constexpr int S = stages<T>();
   constexpr uint32_t SB = stage_bytes<T>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float *epi = (float *)(smem + (size_t)S * SB);
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
-  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_err;
+  __shared__ volatile int s_err;
 
-  const int bid = blockIdx.x;
-  int p = 0;
-  while (p + 1 < g.count && bid >= g.d[p + 1].tile_begin) ++p;
-  const MDesc &d = g.d[p];
-  const int local = bid - d.tile_begin;
-  const int per_split = LOWER ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
-  const int z = local / per_split;
-  const int rem = local - z * per_split;
-  int m0, n0;
-  if (LOWER) {
-    int ti = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
-    while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
-    while (ti * (ti + 1) / 2 > rem) --ti;
-    m0 = ti * BM;
-    n0 = (rem - ti * (ti + 1) / 2) * BN;
-  } else {
-    m0 = (rem / d.tiles_n) * BM;
-    n0 = (rem % d.tiles_n) * BN;
-  }
-  const int kbeg = z * d.kchunk;
-  const int kend = min(d.K, kbeg + d.kchunk);
-  const int nkb = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
+  const int units = g.total_tiles;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], kEpiWarps);
+    }
+    mbar_init(&drain_bar, 1);
     s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {  // two accumulators: the leading term product, and the correction products
+  if (warp == 1) {  // all of tensor memory: two accumulator sets of 2 x BN columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(2 * BN)
+                 "r"(4 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -310,136 +395,168 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer: all terms of A and B for one 64-wide K block per stage.
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (kb >= S && !mbar_wait(&empty_bar[s], (uint32_t)((kb / S) - 1) & 1u)) {
-        s_err = 1;
-        break;
+  if (warp == 0) {
+    uint32_t it = 0;  // K blocks issued by this CTA, over all its units
+    bool ok = true;
+    uint32_t last_it[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) last_it[s] = 0xFFFFFFFFu;
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const Unit x = decode_unit<LOWER>(g, u);
+      const MDesc &d = g.d[x.p];
+      if (d.splits == 1 && d.comb >= kAdd) {
+        const int rows = min(BM, d.M - x.m0), cols = min(BN, d.N - x.n0);
+        for (int r = lane; r < rows; r += 32) {
+          const char *p0 = (const char *)(d.Cin + (long long)(x.m0 + r) * d.ldcin + x.n0);
+          for (int o = 0; o < cols * 8; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + o));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + cols * 8 - 8));
+        }
       }
-      uint8_t *sa = smem + s * SB;
-      uint8_t *sb = sa + T * kTileBytes;
-      mbar_expect_tx(&full_bar[s], SB + (kb == 0 ? (uint32_t)g.tx_extra : 0u));
-      const int kx = kbeg + kb * BK;
-      tma_load_3d(sa, &d.ta, d.ax + kx, d.ay + m0, 0, &full_bar[s]);
-      tma_load_3d(sb, &d.tb, d.bx + kx, d.by + n0, 0, &full_bar[s]);
+      if (lane == 0) {
+        for (int kb = 0; kb < x.nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          if (it >= (uint32_t)S && !mbar_wait_or_abort(&empty_bar[s], ((it / S) - 1) & 1u, &s_err)) {
+            s_err = 1;
+            ok = false;
+            break;
+          }
+          uint8_t *sa = smem + s * SB;
+          uint8_t *sb = sa + T * kTileBytes;
+          mbar_expect_tx(&full_bar[s], SB + (it == 0 ? (uint32_t)g.tx_extra : 0u));
+          const int kx = x.kbeg + kb * BK;
+          tma_load_3d(sa, &d.ta, d.ax + kx, d.ay + x.m0, 0, &full_bar[s]);
+          tma_load_3d(sb, &d.tb, d.bx + kx, d.by + x.n0, 0, &full_bar[s]);
+          last_it[s] = it;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: every kept term product of every 16-wide K step.  The
-    // leading product t0 t0 accumulates alone at columns [0, BN); the smaller
-    // corrections at [BN, 2 BN), so they never round against the large sum.
-    int issued_main = 0, issued_corr = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait(&full_bar[s], (uint32_t)(kb / S) & 1u)) {
+    if (lane == 0 && !ok) {
+      // failure: let copies still in flight land before the CTA exits (bounded)
+      for (int s = 0; s < S; ++s)
+        if (last_it[s] != 0xFFFFFFFFu) {
+          const unsigned long long t0 = globaltimer();
+          while (!mbar_try_wait(&full_bar[s], (last_it[s] / S) & 1u) && globaltimer() - t0 < kTimeoutNs / 8) {
+          }
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      int t = 0;
+      bool issued = false;
+      for (int u = blockIdx.x; u < units; u += gridDim.x, ++t) {
+        const Unit x = decode_unit<LOWER>(g, u);
+        const int b = t & 1;
+        if (t >= 2 && !mbar_wait_or_abort(&tempty_bar[b], (uint32_t)((t >> 1) - 1) & 1u, &s_err)) {
+          s_err = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * 2 * BN);
+        int issued_main = 0, issued_corr = 0;
+        bool ok = true;
+        for (int kb = 0; kb < x.nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          if (!mbar_wait_or_abort(&full_bar[s], (it / S) & 1u, &s_err)) {
+            s_err = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * SB);
+          const uint32_t sb = sa + T * kTileBytes;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+            for (int q = 0; q < Terms<T>::n; ++q) {
+              const int ta = Terms<T>::a(q), tb = Terms<T>::b(q);
+              const uint64_t ad = sw128_desc(sa + ta * kTileBytes + kk * 32);
+              const uint64_t bd = sw128_desc(sb + tb * kTileBytes + kk * 32);
+              if (ta == 0 && tb == 0) {
+                mma_bf16(acc, ad, bd, issued_main ? 1u : 0u);
+                issued_main = 1;
+              } else {
+                mma_bf16(acc + BN, ad, bd, issued_corr ? 1u : 0u);
+                issued_corr = 1;
+              }
+            }
+          }
+          issued = true;
+          mma_commit(&empty_bar[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull_bar[b]);
+      }
+      if (s_err && issued) {  // failure: products already issued finish before tensor memory is freed
+        mma_commit(&drain_bar);
+        mbar_wait(&drain_bar, 0);
+      }
+    }
+    __syncwarp();
+  } else {
+    // Epilogue.  Tensor-memory lanes are reachable from warp w in quarter w % 4.
+    const int qd = warp & 3;
+    const int half = (warp - 2) / 4;  // columns [64 half, 64 half + 64)
+    float *stw = epi + (size_t)(warp - 2) * 32 * kEpiLd;
+    int t = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++t) {
+      const Unit x = decode_unit<LOWER>(g, u);
+      const MDesc &d = g.d[x.p];
+      const int b = t & 1;
+      const bool got = mbar_wait_or_abort(&tfull_bar[b], (uint32_t)(t >> 1) & 1u, &s_err);
+      if (!__all_sync(0xffffffffu, got)) {
         s_err = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * SB);
-      const uint32_t sb = sa + T * kTileBytes;
+      const uint32_t acc = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 2 * BN);
+      const int rbase = x.m0 + qd * 32;  // this warp's 32 rows
+      const int nrows = max(0, min(32, d.M - rbase));
+      const int comb = d.comb;
+#pragma unroll 1
+      for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+        uint32_t r[32], q[32];
+        tmem_ld32(acc + (uint32_t)c0, r);
+        tmem_ld32(acc + (uint32_t)(BN + c0), q);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-#pragma unroll
-        for (int q = 0; q < Terms<T>::n; ++q) {
-          const int ta = Terms<T>::a(q), tb = Terms<T>::b(q);
-          const uint64_t ad = sw128_desc(sa + ta * kTileBytes + kk * 32);
-          const uint64_t bd = sw128_desc(sb + tb * kTileBytes + kk * 32);
-          if (ta == 0 && tb == 0) {
-            mma_bf16(tmem, ad, bd, issued_main ? 1u : 0u);
-            issued_main = 1;
+        for (int i = 0; i < 32; ++i)
+          stw[lane * kEpiLd + i] = x.nkb > 0 ? __uint_as_float(r[i]) + __uint_as_float(q[i]) : 0.0f;
+        __syncwarp();
+        // lane = output column; the warp writes its rows one at a time, coalesced
+        const int j = x.n0 + c0 + lane;
+        if (j < d.N && x.n0 + c0 < d.N) {
+          if (d.splits > 1) {
+            for (int rr = 0; rr < nrows; ++rr) {
+              const int i = rbase + rr;
+              if (!(LOWER && j > i)) d.part[((long long)x.z * d.M + i) * d.N + j] = stw[rr * kEpiLd + lane];
+            }
           } else {
-            mma_bf16(tmem + BN, ad, bd, issued_corr ? 1u : 0u);
-            issued_corr = 1;
+            write_column_any<LOWER>(comb, d, stw + lane, kEpiLd, rbase, nrows, j);
           }
         }
+        __syncwarp();
       }
-      mma_commit(&empty_bar[s]);
-    }
-    mma_commit(&done_bar);
-  }
-  __syncwarp();
-
-  // Epilogue: accumulators (FP32, tensor memory) -> their FP32 sum, staged
-  // in shared memory -> FP64 output with one FP64 operation per element.
-  // The corrections were accumulated apart from the leading product; adding
-  // the two once here rounds once at 2^-24, far below the accumulation's own
-  // rounding over K.
-  if (!mbar_wait(&done_bar, 0)) s_err = 1;
-  tc_fence_after();
-  __syncthreads();
-  const bool err = s_err != 0;
-  float *stage = (float *)smem;
-  constexpr int LDS = BN + 1;
-  if (!err) {
-    const int row = warp * 32 + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32], q[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(BN + c0), q);
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        stage[row * LDS + c0 + i] = nkb > 0 ? __uint_as_float(r[i]) + __uint_as_float(q[i]) : 0.0f;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[b]);
     }
   }
-  tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * BN) : "memory");
   }
-  if (err) {
-    if (threadIdx.x == 0 && g.err) atomicExch(g.err, CD_ETIMEOUT);
-    return;
-  }
-  // Each thread owns one output column; rows go in chunks of 16 whose Cin
-  // values are all loaded before any is stored (Cin may alias Cout, and a
-  // thread only ever rewrites the elements it has read), so the loads of a
-  // chunk are in flight together instead of one global round trip per row.
-  const int j = n0 + threadIdx.x;
-  const bool col_ok = j < d.N;
-  const int rows = min(BM, d.M - m0);
-  if (d.splits > 1) {  // FP32 partial sums; the reduction forms the FP64 output
-    if (col_ok)
-      for (int r = 0; r < rows; ++r) {
-        const int i = m0 + r;
-        if (!(LOWER && j > i)) d.part[((long long)z * d.M + i) * d.N + j] = stage[r * LDS + threadIdx.x];
-      }
-    return;
-  }
-  const int comb = d.comb;
-  const double alpha = d.alpha, beta = d.beta;
-  const bool use_cin = comb >= kAdd;
-  constexpr int CH = 16;
-  for (int r0 = 0; r0 < rows; r0 += CH) {
-    double cin[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int r = r0 + q, i = m0 + r;
-      cin[q] = 0.0;
-      if (use_cin && col_ok && r < rows && !(LOWER && j > i)) cin[q] = d.Cin[(long long)i * d.ldcin + j];
-    }
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int r = r0 + q, i = m0 + r;
-      if (!col_ok || r >= rows || (LOWER && j > i)) continue;
-      d.Cout[(long long)i * d.ldcout + j] = combine(comb, f32_to_f64(stage[r * LDS + threadIdx.x]), cin[q], alpha, beta);
-    }
-  }
+  if (threadIdx.x == 0 && s_err && g.err) atomicExch(g.err, CD_ETIMEOUT);
 }
 
 // Split-K reduction: the FP32 partials, in order, by compensated summation
 // in FP32 (Neumaier's variant of Kahan summation: the rounding error of each
 // addition, obtained exactly, is carried in c), then s + c to FP64 and the
-// output formed as in the product's epilogue.
-template <bool LOWER>
-__global__ void k_mreduce(const __grid_constant__ MGroup g) {
-  const MDesc &d = g.d[blockIdx.y];
-  if (d.splits <= 1) return;
+// output formed as in the product's epilogue (mode fixed per loop, as there).
+template <int COMB, bool LOWER>
+__device__ __forceinline__ void reduce_loop(const MDesc &d) {
   const long long total = (long long)d.M * d.N;
-  const int comb = d.comb;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / d.N), j = (int)(e - (long long)i * d.N);
@@ -452,8 +569,23 @@ __global__ void k_mreduce(const __grid_constant__ MGroup g) {
       s = t;
     }
     const double a = f32_to_f64(s) + f32_to_f64(c);
-    const double cin = comb >= kAdd ? d.Cin[(long long)i * d.ldcin + j] : 0.0;
-    d.Cout[(long long)i * d.ldcout + j] = combine(comb, a, cin, d.alpha, d.beta);
+    const double cin = COMB >= kAdd ? d.Cin[(long long)i * d.ldcin + j] : 0.0;
+    d.Cout[(long long)i * d.ldcout + j] = combine<COMB>(a, cin, d.alpha, d.beta);
+  }
+}
+
+template <bool LOWER>
+__global__ void k_mreduce(const __grid_constant__ MGroup g) {
+  const MDesc &d = g.d[blockIdx.y];
+  if (d.splits <= 1) return;
+  switch (d.comb) {
+    case kCopy: reduce_loop<kCopy, LOWER>(d); break;
+    case kNeg: reduce_loop<kNeg, LOWER>(d); break;
+    case kScale: reduce_loop<kScale, LOWER>(d); break;
+    case kAdd: reduce_loop<kAdd, LOWER>(d); break;
+    case kSub: reduce_loop<kSub, LOWER>(d); break;
+    case kAxpy: reduce_loop<kAxpy, LOWER>(d); break;
+    default: reduce_loop<kGeneral, LOWER>(d); break;
   }
 }
 
@@ -530,9 +662,28 @@ bool encode_map(CUtensorMap *m, const MOp &op) {
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Units per CTA at most: a persistent CTA holds its SM until its last unit,
+// so a long product launched on the bulk stream must still hand SMs back
+// every few tiles to the diagonal chain's launches on the high-priority stream.
+constexpr int kMaxUnitsPerCta = 4;
+
+int sm_count() {
+  static int cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 template <int T, bool LOWER>
 cudaError_t launch_one(const MGroup &g, cudaStream_t s) {
-  k_mgemm<T, LOWER><<<g.total_tiles, kThreads, dyn_smem<T>(), s>>>(g);
+  const int units = g.total_tiles;
+  const int grid = std::min(units, std::max(sm_count(), (units + kMaxUnitsPerCta - 1) / kMaxUnitsPerCta));
+  k_mgemm<T, LOWER><<<grid, kThreads, dyn_smem<T>(), s>>>(g);
   return cudaGetLastError();
 }
 
