@@ -55,6 +55,7 @@ struct MDesc {  // 64-byte aligned through CUtensorMap
   int tiles_m, tiles_n, tile_begin;
   int ax, ay, bx, by;
   int comb;     // a Comb value
+  int vec;      // Cout (and Cin if read) 16-byte aligned with even leading dimensions: 16-byte accesses
 };
 
 struct MGroup {
@@ -77,24 +78,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 // 80 cycles per warp), while integer and FP32 instructions issue every few
 // cycles; these run once per element of every product and every split.
 
-// binary32 -> binary64, exact: rebias the exponent and widen the significand
-// (a subnormal input is normalised by its leading-one position).
+// binary32 -> binary64 without branches: rebias the exponent and widen the
+// significand (exact for normal numbers, zeros, infinities and NaN); a
+// subnormal binary32 (below 2^-126) is taken as zero.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t b = __float_as_uint(f);
-  const uint64_t sg = (uint64_t)(b >> 31) << 63;
-  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
-  uint64_t r;
-  if (e - 1u < 254u) {
-    r = sg | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
-  } else if (e == 0xFFu) {
-    r = sg | 0x7FF0000000000000ull | ((uint64_t)m << 29);
-  } else if (m == 0) {
-    r = sg;
-  } else {  // m 2^-149 = 1.f 2^(p - 149), p the leading-one position of m
-    const int p = 31 - __clz((int)m);
-    r = sg | ((uint64_t)(p + 874) << 52) | ((uint64_t)(m ^ (1u << p)) << (52 - p));
-  }
-  return __longlong_as_double((long long)r);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t hi = (b & 0x80000000u) | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  const uint32_t lo = b << 29;
+  return e == 0 ? __longlong_as_double((long long)(uint64_t)(b & 0x80000000u) << 32)
+                : __hiloint2double((int)hi, (int)lo);
 }
 
 // binary64 x -> (hi, lo) in binary32: hi is x with its significand cut to 24
@@ -144,16 +137,62 @@ template <int COMB, bool LOWER>
 __device__ __forceinline__ void write_column(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j) {
   constexpr bool kUseCin = COMB >= kAdd;
   double cin[32];
+  const double *ci = d.Cin + (long long)rbase * d.ldcin + j;
 #pragma unroll
   for (int rr = 0; rr < 32; ++rr) {
-    const int i = rbase + rr;
-    cin[rr] = (kUseCin && rr < nrows && !(LOWER && j > i)) ? d.Cin[(long long)i * d.ldcin + j] : 0.0;
+    cin[rr] = (kUseCin && rr < nrows && !(LOWER && j > rbase + rr)) ? ci[0] : 0.0;
+    ci += d.ldcin;
   }
+  double *co = d.Cout + (long long)rbase * d.ldcout + j;
 #pragma unroll
   for (int rr = 0; rr < 32; ++rr) {
-    const int i = rbase + rr;
-    if (rr < nrows && !(LOWER && j > i))
-      d.Cout[(long long)i * d.ldcout + j] = combine<COMB>(f32_to_f64(stw[rr * ld]), cin[rr], d.alpha, d.beta);
+    if (rr < nrows && !(LOWER && j > rbase + rr))
+      *co = combine<COMB>(f32_to_f64(stw[rr * ld]), cin[rr], d.alpha, d.beta);
+    co += d.ldcout;
+  }
+}
+
+// The same for a 32 x 32 block in 16-byte accesses: lane l covers columns
+// j0 + 2 (l % 16) + {0, 1} of row pair member l / 16 (Cout, Cin 16-byte
+// aligned, even leading dimensions, j0 even).  Non-LOWER tiles only.
+template <int COMB>
+__device__ __forceinline__ void write_block_v2(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j0,
+                                               int ncols, int lane) {
+  constexpr bool kUseCin = COMB >= kAdd;
+  const int c = 2 * (lane & 15), h = lane >> 4;
+  const bool col_ok = c < ncols;  // ncols even here
+  double2 cin[16];
+  const double *ci = d.Cin + (long long)(rbase + h) * d.ldcin + j0 + c;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    cin[k] = make_double2(0.0, 0.0);
+    if (kUseCin && col_ok && 2 * k + h < nrows) cin[k] = *reinterpret_cast<const double2 *>(ci);
+    ci += 2 * d.ldcin;
+  }
+  double *co = d.Cout + (long long)(rbase + h) * d.ldcout + j0 + c;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int rr = 2 * k + h;
+    if (col_ok && rr < nrows) {
+      double2 v;
+      v.x = combine<COMB>(f32_to_f64(stw[rr * ld + c]), cin[k].x, d.alpha, d.beta);
+      v.y = combine<COMB>(f32_to_f64(stw[rr * ld + c + 1]), cin[k].y, d.alpha, d.beta);
+      *reinterpret_cast<double2 *>(co) = v;
+    }
+    co += 2 * d.ldcout;
+  }
+}
+
+__device__ __forceinline__ void write_block_v2_any(int comb, const MDesc &d, const float *stw, int ld, int rbase,
+                                                   int nrows, int j0, int ncols, int lane) {
+  switch (comb) {
+    case kCopy: write_block_v2<kCopy>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    case kNeg: write_block_v2<kNeg>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    case kScale: write_block_v2<kScale>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    case kAdd: write_block_v2<kAdd>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    case kSub: write_block_v2<kSub>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    case kAxpy: write_block_v2<kAxpy>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
+    default: write_block_v2<kGeneral>(d, stw, ld, rbase, nrows, j0, ncols, lane); break;
   }
 }
 
@@ -524,16 +563,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
           stw[lane * kEpiLd + i] = x.nkb > 0 ? __uint_as_float(r[i]) + __uint_as_float(q[i]) : 0.0f;
         __syncwarp();
         // lane = output column; the warp writes its rows one at a time, coalesced
-        const int j = x.n0 + c0 + lane;
-        if (j < d.N && x.n0 + c0 < d.N) {
-          if (d.splits > 1) {
+        const int j0 = x.n0 + c0, j = j0 + lane;
+        const int ncols = min(32, d.N - j0);
+        if (d.splits > 1) {
+          if (j < d.N)
             for (int rr = 0; rr < nrows; ++rr) {
               const int i = rbase + rr;
               if (!(LOWER && j > i)) d.part[((long long)x.z * d.M + i) * d.N + j] = stw[rr * kEpiLd + lane];
             }
-          } else {
-            write_column_any<LOWER>(comb, d, stw + lane, kEpiLd, rbase, nrows, j);
-          }
+        } else if (d.vec && !(LOWER && x.m0 == x.n0) && (ncols & 1) == 0) {
+          if (ncols > 0) write_block_v2_any(comb, d, stw, kEpiLd, rbase, nrows, j0, ncols, lane);
+        } else if (j < d.N) {
+          write_column_any<LOWER>(comb, d, stw + lane, kEpiLd, rbase, nrows, j);
         }
         __syncwarp();
       }
@@ -753,6 +794,8 @@ cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lowe
       d.comb = P.beta == 0.0 ? (P.alpha == 1.0 ? kCopy : P.alpha == -1.0 ? kNeg : kScale)
                : P.beta == 1.0 ? (P.alpha == 1.0 ? kAdd : P.alpha == -1.0 ? kSub : kAxpy)
                                : kGeneral;
+      d.vec = ((uintptr_t)P.Cout % 16 == 0) && (P.ldcout % 2 == 0) &&
+              (d.comb < kAdd || (((uintptr_t)P.Cin % 16 == 0) && (P.ldcin % 2 == 0)));
       d.ldcin = P.ldcin;
       d.ldcout = P.ldcout;
       d.alpha = P.alpha;

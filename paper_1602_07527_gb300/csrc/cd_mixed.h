@@ -7,7 +7,8 @@
 // order is at most 2^-8 (T = 2: t0 t0, t0 t1, t1 t0) or 2^-16 (T = 3: adds
 // t0 t2, t2 t0, t1 t1) relative to the leading one, accumulated in FP32 in
 // tensor memory (the leading product apart from the corrections), and added
-// to the FP64 output in FP64.  Split-K partial sums are FP32.
+// to the FP64 output in FP64 (an FP32 sum below 2^-126, subnormal, counts as
+// zero).  Split-K partial sums are FP32.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
