@@ -80,7 +80,51 @@ def parse():
     ap.add_argument("--serve-lanes", type=int, default=2)
     ap.add_argument("--serve-sustained-rate", type=float, default=250.0,
                     help="a second, sustainable arrival rate (about 80%% of measured capacity)")
+    ap.add_argument("--profile-pass", default=None, choices=["fwd", "sens", "rev", "fwd_and_sens"],
+                    help="for profilers: run one pass of this operation on the --n workload and exit "
+                         "(no timing, no JSON line); the factor it needs is computed first in FP64")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6"],
+                    help="precision of the --profile-pass operation")
     return ap.parse_args()
+
+
+def profile_pass(args):
+    """One pass of one operation, for a profiler to capture: the FP64 SE workload
+    for --prec fp64, the Matern-5/2 workload for the split-BF16 precisions."""
+    import torch
+    import paper_1602_07527_gb300 as cd
+    from paper_1602_07527_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    n = args.n
+    if args.prec == "fp64":
+        S, Lb = W.large_se_case(n, SE_SEED)
+        seed = SE_SEED
+    else:
+        S, Lb = W.mixed_matern_case(n, 3)
+        seed = 3
+    A = torch.tensor(np.tril(S), device=dev)
+    del S
+    op = args.profile_pass
+    if op in ("fwd", "fwd_and_sens"):
+        if op == "fwd":
+            info = cd.chol_fwd(A, nb=args.nb, prec=args.prec)
+        else:
+            Ad = torch.tensor(np.tril(W.sigma_dot(n, seed)), device=dev)
+            info = cd.chol_fwd_and_sens(A, Ad, nb=args.nb, prec=args.prec, diag=args.diag)
+    else:
+        info = cd.chol_fwd(A)  # the FP64 factor the derivative pass takes as input
+        if op == "rev":
+            X = torch.tensor(Lb, device=dev)
+            cd.chol_rev(A, X, nb=args.nb, prec=args.prec, diag=args.diag)
+        else:
+            X = torch.tensor(np.tril(W.sigma_dot(n, seed)), device=dev)
+            cd.chol_fwd_sens(A, X, nb=args.nb, prec=args.prec, diag=args.diag)
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError("factorisation reported a non-positive pivot")
+    print(f"profile pass done: {op} {args.prec} N={n}", file=sys.stderr)
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -535,6 +579,8 @@ def serve_bench(args, dev):
 
 def main():
     args = parse()
+    if args.profile_pass:
+        return profile_pass(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
