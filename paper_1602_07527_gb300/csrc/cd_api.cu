@@ -329,7 +329,7 @@ struct TileBatch {
   }
   void flush() {
     if (g.count == 0) return;
-    static const char *names[4] = {"tile_potf2", "tile_rev", "tile_sens", "tile_trtri"};
+    static const char *names[5] = {"tile_potf2", "tile_rev", "tile_sens", "tile_trtri_cluster", "tile_potrf_cluster"};
     double flops = 0, bytes = 0;
     for (int p = 0; p < g.count; ++p) {
       const double t = g.d[p].t, tri = 0.5 * t * (t + 1) * 8.0;
@@ -338,6 +338,7 @@ struct TileBatch {
         case T_REV: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
         case T_SENS: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
         case T_TRTRI: flops += t * t * t / 3.0; bytes += tri + 8 * t * t; break;
+        case T_POTRF: flops += t * t * t / 3.0 * (g.d[p].inv ? 2.0 : 1.0); bytes += 2 * tri + (g.d[p].inv ? 8 * t * t : 0); break;
       }
     }
     c.launch(names[op], flops, bytes, [&] { return launch_tile_group(op, g, c.s); });
@@ -588,16 +589,14 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f2: D <- chol_unblocked(D); then the inverse of D for f4
-      TileBatch tb(c, T_POTF2);
-      TileBatch ti(c, T_TRTRI);
+      TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
-          if (k < p.n) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, k < p.n ? p.dinv : nullptr, nb, w, p.info, p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -609,8 +608,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
-      tb.flush();  // the factorisations first, then the inverses of their results
-      ti.flush();
+      tb.flush();
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}   (W = C Dinv^T, then copy back)
@@ -902,16 +900,15 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f2: D <- chol_unblocked(D) and its inverse (wide blocks: both diagonal steps by recursion)
-      TileBatch tb(c, T_POTF2);
-      TileBatch ti(c, T_TRTRI);
+      TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
-          if (k < p.n || diag_symbolic(c, p, nb)) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, (k < p.n || diag_symbolic(c, p, nb)) ? p.dinv : nullptr, nb, w, p.info,
+                       p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -925,8 +922,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
-      tb.flush();  // the factorisations first, then the inverses of their results
-      ti.flush();
+      tb.flush();
     }
     {  // g2 as the products of Eq. symfwd (problems that use them)
       std::vector<DiagRev> v;
@@ -1345,16 +1341,14 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
-      TileBatch tb(c, T_POTF2);
-      TileBatch ti(c, T_TRTRI);
+      TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
-          if (j + w < p.n) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, j + w < p.n ? p.dinv : nullptr, nb, w, p.info, p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -1366,8 +1360,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
-      tb.flush();  // the factorisations first, then the inverses of their results
-      ti.flush();
+      tb.flush();
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}
@@ -1602,16 +1595,15 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     {  // f2: D <- chol_unblocked(D) and its inverse, FP64 (wide blocks: both diagonal steps by recursion)
-      TileBatch tb(c, T_POTF2);
-      TileBatch ti(c, T_TRTRI);
+      TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, nullptr, 0, w, p.info, p.col0 + j));
-          if (k < p.n || diag_symbolic(c, p, nb)) ti.add(tdesc(D, p.ldx, nullptr, 0, p.dinv, nb, w));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, (k < p.n || diag_symbolic(c, p, nb)) ? p.dinv : nullptr, nb, w, p.info,
+                       p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -1625,8 +1617,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           ar.off = mark;
         }
       }
-      tb.flush();  // the factorisations first, then the inverses of their results
-      ti.flush();
+      tb.flush();
     }
     {  // g2 as the products of Eq. symfwd (FP64)
       std::vector<DiagRev> v;

@@ -7,7 +7,9 @@
 // 1.19 TFLOP/s for the whole GPU, 8 GFLOP/s on one SM), and DMMA
 // (mma.sync f64) is slower still, so the FP64 engine is a register-blocked
 // DFMA kernel: its only job is to keep the FP64 pipe of every SM busy.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -440,6 +442,263 @@ cudaError_t launch_trtri_group(const TileGroup &g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal tile on a thread-block cluster: chol_unblocked (Sec. 4.1) of a
+// t x t tile (t <= 128) and the inverse of the factor, or the inverse alone.
+//
+// On GB300 every FP64 instruction holds its sub-partition's FP64 unit for
+// about 64 cycles and a square root or division about 650, so a one-CTA
+// factorisation of a 128 tile takes ~265 us: its 128 sequential pivots and
+// the t^3/6 multiply-adds of its updates all run on one SM.  Here kCl CTAs
+// (one SM each) share the tile through distributed shared memory: rows are
+// dealt cyclically (row i to CTA i mod kCl); every CTA holds a full copy of
+// L as it is finished.  The tile is factorised right-looking in 16-column
+// panels (chol_blocked of Sec. 4.2 inside the tile):
+//   (a) the owners of the panel's diagonal-block rows send them to all CTAs;
+//   (b) every CTA factorises that block redundantly with four warps (one per
+//       sub-partition): per column one reciprocal square root by Goldschmidt's
+//       iteration (seven FP64 operations instead of a square root and a
+//       division), then the column scaled and the block's trailing entries
+//       updated one per thread -- all CTAs take the same pivot decisions;
+//   (c) each CTA solves its own rows of the panel, C <- C D^{-T}, by forward
+//       substitution across the 16 lanes of a half-warp (each step: one
+//       multiply by the pivot's reciprocal, a shuffle, one multiply-add), and
+//       sends them to every CTA's copy of L;
+//   (d) each CTA applies the rank-16 update to its own trailing rows.
+// Two cluster barriers per panel.  The inverse then needs one exchange: CTA b
+// inverts diagonal block b (a forward-substitution sweep per column, again
+// across half-warps) and sends it to all; each CTA then forms its own columns
+// of X = L^{-1} block row by block row, X_bi = D_bi^{-1} (E - L_{bi,<bi} X_{<bi}).
+// ---------------------------------------------------------------------------
+constexpr int kCl = 8;                     // CTAs per tile (portable cluster size)
+constexpr int kPb = 16;                    // panel width
+constexpr int kOwn = kTileMax / kCl;       // rows (and inverse columns) per CTA
+constexpr int kNpMax = kTileMax / kPb;     // panels per tile
+constexpr int kPotrfThreads = 256;
+constexpr int kLfN = kTileMax * (kTileMax + 1) / 2;
+constexpr int kDgLd = kPb + 1;
+static_assert(kOwn == kPb && kOwn * kPb == kPotrfThreads && kNpMax <= kCl, "thread layout");
+constexpr size_t kPotrfSmem = sizeof(double) * (kLfN + kOwn * kTileMax + kPb * kDgLd + kTileMax +
+                                                kNpMax * kPb * kPb + kTileMax * kOwn + kPb * kOwn);
+
+// Exact binary32 -> binary64 of a normal positive float, with integer operations.
+__device__ __forceinline__ double pos_f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = b >> 23;
+  return __hiloint2double((int)(((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+}
+
+// v * 2^k by the exponent field (v normal, result normal).
+__device__ __forceinline__ double scale_pow2(double v, int k) {
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)k << 52));
+}
+
+// 1/sqrt(x) and sqrt(x) for a positive FP64 x by Goldschmidt's iteration
+// (g -> sqrt(m), h -> 1/(2 sqrt(m)); r = 1/2 - g h, g += g r, h += h r),
+// started from the FP32 hardware estimate of 1/sqrt(m), m = x 2^(-2k) in
+// [1, 4).  Two iterations take the 2^-23 start below FP64 rounding.
+// Subnormal and infinite x take the library square root.
+__device__ __forceinline__ void rsqrt_sqrt(double x, double &rs, double &sq) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52) & 0x7FF;
+  if (e == 0 || e == 0x7FF) {
+    sq = sqrt(x);
+    rs = 1.0 / sq;
+    return;
+  }
+  const int k = (e - 1023) >> 1;
+  const unsigned long long em = (unsigned long long)(e - 2 * k);  // 1023 or 1024
+  const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | (em << 52)));
+  const float mf = __uint_as_float((unsigned)((em - 896ull) << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+  const double y = pos_f32_to_f64(rsqrtf(mf));
+  double g = m * y, h = scale_pow2(y, -1);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+  }
+  sq = scale_pow2(g, k);
+  rs = scale_pow2(h, 1 - k);
+}
+
+// Inverse of the lower kPb x kPb block of Lf at (c0, c0) (w x w used, rest
+// zero) into Li (row major), given the reciprocals rd of its diagonal.  All
+// 256 threads: half-warp q (16 lanes = rows) sweeps column q forward.
+__device__ void block_inverse_sweep(const double *Lf, const double *rd, int c0, int w, double *Li) {
+  const int lane16 = threadIdx.x & 15, col = threadIdx.x >> 4;  // 16 half-warps = 16 columns
+  const int r = lane16;
+  double x = (r == col && r < w) ? rd[c0 + r] : 0.0, acc = 0.0;
+  for (int s = 0; s < kPb; ++s) {
+    if (s > col && r == s && r < w) x = -acc * rd[c0 + r];
+    const double xs = __shfl_sync(0xffffffffu, x, s, 16);
+    if (r > s && s >= col && r < w) acc = fma(Lf[pk(c0 + r, c0 + s)], xs, acc);
+  }
+  Li[r * kPb + col] = (r >= col && r < w && col < w) ? x : 0.0;
+}
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
+    k_potrf_cluster(const __grid_constant__ TileGroup g) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double sm[];
+  __shared__ int s_bad;
+  const TileDesc &d = g.d[blockIdx.y];
+  const int t = d.t;
+  // Both exits below are taken by every CTA of the cluster alike (same
+  // descriptor; info is written only by earlier launches), before any barrier.
+  if (t <= 0 || t > kTileMax) return;
+  const bool factor = d.X != nullptr;
+  if (factor && d.info != nullptr && *(volatile int *)d.info != 0) return;  // an earlier column failed
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  double *Lf = sm;                          // packed L, every row (each CTA holds a full copy)
+  double *R = Lf + kLfN;                    // own rows i = rank + kCl * li, R[li * kTileMax + k]
+  double *Dg = R + kOwn * kTileMax;         // the panel's diagonal block, kPb x kDgLd
+  double *rd = Dg + kPb * kDgLd;            // reciprocals of L's diagonal
+  double *Li = rd + kTileMax;               // inverses of the diagonal blocks, [block][kPb][kPb]
+  double *Xc = Li + kNpMax * kPb * kPb;     // own inverse columns c = rank + kCl * q: Xc[r * kOwn + q]
+  double *Yt = Xc + kTileMax * kOwn;        // kPb x kOwn temporary
+  const int nown = rank < t ? (t - 1 - rank) / kCl + 1 : 0;
+  const int np = (t + kPb - 1) / kPb;
+  if (tid == 0) s_bad = -1;
+
+  if (factor) {
+    for (int e = tid; e < nown * kTileMax; e += blockDim.x) {
+      const int li = e / kTileMax, k = e - li * kTileMax, i = rank + kCl * li;
+      if (k <= i) R[e] = d.X[(long long)i * d.ldx + k];
+    }
+    cluster.sync();  // every CTA resident (its shared memory exists) before any remote store
+    for (int p = 0; p < np; ++p) {
+      const int c0 = p * kPb, w = min(kPb, t - c0);
+      {  // (a) own rows of the diagonal block (c0 + rank and c0 + rank + kCl) to every CTA
+        const int slot = tid / (kPb * kCl), c = (tid / kCl) % kPb, dst = tid % kCl;
+        const int i = c0 + rank + kCl * slot;
+        if (slot < 2 && i < c0 + w && c0 + c <= i) {
+          double *rem = cluster.map_shared_rank(Dg, dst);
+          rem[(i - c0) * kDgLd + c] = R[((i - rank) / kCl) * kTileMax + c0 + c];
+        }
+      }
+      cluster.sync();
+      if (tid < 128) {  // (b) chol_unblocked of the block by warps 0-3, redundantly in every CTA
+        for (int c = 0; c < w; ++c) {
+          const double piv = Dg[c * kDgLd + c];
+          const long long pb = __double_as_longlong(piv);
+          const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;  // piv > 0 (false for NaN)
+          double rs = 0.0, sq = piv;
+          if (ok) rsqrt_sqrt(piv, rs, sq);
+          const int m = w - c - 1;
+          if (tid == 0) {
+            Lf[pk(c0 + c, c0 + c)] = ok ? sq : piv;
+            rd[c0 + c] = rs;
+            if (!ok && s_bad < 0) s_bad = c0 + c;
+          }
+          if (tid < m) Lf[pk(c0 + c + 1 + tid, c0 + c)] = Dg[(c + 1 + tid) * kDgLd + c] * rs;
+          if (tid < m * (m + 1) / 2) {  // trailing pair (r, k), c < k <= r < w
+            const int rr = tri_row(tid), kk = tid - rr * (rr + 1) / 2;
+            const int r = c + 1 + rr, k = c + 1 + kk;
+            const double arc = Dg[r * kDgLd + c] * (rs * rs);
+            Dg[r * kDgLd + k] = fma(-arc, Dg[k * kDgLd + c], Dg[r * kDgLd + k]);
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+      }
+      __syncthreads();
+      if (s_bad >= 0) break;  // the same in every CTA: all factorised the same block
+      {  // (c) own rows below the block: forward substitution across each half-warp
+        const int li = tid / kPb, c = tid % kPb, i = rank + kCl * li;
+        const bool act = li < nown && i >= c0 + w;
+        double acc = act && c < w ? R[li * kTileMax + c0 + c] : 0.0, lic = 0.0;
+        // a warp whose two rows are both above the panel or absent has nothing to solve
+        if (__any_sync(0xffffffffu, act))
+          for (int s2 = 0; s2 < w; ++s2) {
+          const double v = (c == s2) ? acc * rd[c0 + s2] : 0.0;
+          const double ls = __shfl_sync(0xffffffffu, v, s2, 16);
+          if (c == s2) lic = ls;
+          if (c > s2 && c < w) acc = fma(-ls, Lf[pk(c0 + c, c0 + s2)], acc);
+        }
+        if (act && c < w) {
+          R[li * kTileMax + c0 + c] = lic;
+#pragma unroll
+          for (int dst = 0; dst < kCl; ++dst) cluster.map_shared_rank(Lf, dst)[pk(i, c0 + c)] = lic;
+        }
+      }
+      cluster.sync();  // every CTA's Lf holds the panel's columns of L
+      {  // (d) rank-kPb update of own trailing rows, 16 threads per row
+        const int li = tid / kPb, i = rank + kCl * li;
+        if (li < nown && i >= c0 + w) {
+          double lrow[kPb];
+#pragma unroll
+          for (int c = 0; c < kPb; ++c) lrow[c] = R[li * kTileMax + c0 + c];
+          for (int k = c0 + w + (tid % kPb); k <= i; k += kPb) {
+            const double *lk = Lf + pk(k, c0);
+            double v = R[li * kTileMax + k];
+#pragma unroll
+            for (int c = 0; c < kPb; ++c) v = fma(-lrow[c], lk[c], v);
+            R[li * kTileMax + k] = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    cluster.sync();
+    if (s_bad >= 0) {
+      if (rank == 0 && tid == 0 && d.info != nullptr) *d.info = d.col0 + s_bad + 1;
+      return;  // no remote store follows: each CTA may finish on its own
+    }
+    for (int e = tid; e < nown * kTileMax; e += blockDim.x) {
+      const int li = e / kTileMax, k = e - li * kTileMax, i = rank + kCl * li;
+      if (k <= i) d.X[(long long)i * d.ldx + k] = Lf[pk(i, k)];
+    }
+    if (d.inv == nullptr) return;  // no remote store follows
+  } else {
+    tile_load(Lf, d.L, d.ldl, t);
+    __syncthreads();
+    for (int i = tid; i < t; i += blockDim.x) rd[i] = 1.0 / Lf[pk(i, i)];
+    cluster.sync();  // every CTA resident before the block inverses are exchanged
+  }
+  // Inverse.  CTA b inverts diagonal block b and sends it to every CTA.
+  if (rank < np) {
+    const int c0 = rank * kPb;
+    __syncthreads();
+    block_inverse_sweep(Lf, rd, c0, min(kPb, t - c0), Yt);  // Yt: kPb x kPb scratch here
+    __syncthreads();
+    for (int e = tid; e < kPb * kPb * kCl; e += blockDim.x) {
+      const int dst = e / (kPb * kPb), o = e - dst * kPb * kPb;
+      cluster.map_shared_rank(Li, dst)[rank * kPb * kPb + o] = Yt[o];
+    }
+  }
+  cluster.sync();  // every CTA holds every block inverse; no remote store follows
+  const int rr = tid / kOwn, q = tid % kOwn, c = rank + kCl * q;
+  for (int bi = 0; bi < np; ++bi) {
+    const int r0 = bi * kPb, wb = min(kPb, t - r0), r = r0 + rr;
+    double y = 0.0;
+    if (rr < wb && c < t && c <= r) {
+      y = (r == c) ? 1.0 : 0.0;
+      for (int k = c; k < r0; ++k) y = fma(-Lf[pk(r, k)], Xc[k * kOwn + q], y);
+    }
+    Yt[rr * kOwn + q] = y;
+    __syncthreads();
+    if (rr < wb) {
+      double x = 0.0;
+      const double *Lb = Li + bi * kPb * kPb + rr * kPb;
+      for (int r2 = 0; r2 <= rr; ++r2) x = fma(Lb[r2], Yt[r2 * kOwn + q], x);
+      Xc[r * kOwn + q] = x;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < t * kOwn; e += blockDim.x) {
+    const int r2 = e / kOwn, qq = e - r2 * kOwn, cc = rank + kCl * qq;
+    if (cc < t) d.inv[(long long)r2 * d.ldinv + cc] = (cc <= r2) ? Xc[e] : 0.0;
+  }
+}
+
+cudaError_t launch_potrf_cluster_group(const TileGroup &g, cudaStream_t s) {
+  if (g.count <= 0) return cudaSuccess;
+  k_potrf_cluster<<<dim3(kCl, (unsigned)g.count), kPotrfThreads, kPotrfSmem, s>>>(g);
+  return cudaGetLastError();
+}
+
 cudaError_t tile_kernels_init() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_tile<T_POTF2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
@@ -449,6 +708,8 @@ cudaError_t tile_kernels_init() {
   if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;
   if ((e = cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem))) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem)))
+    return e;
   return cudaSuccess;
 }
 
@@ -458,7 +719,8 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
     case T_POTF2: k_tile<T_POTF2><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_REV: k_tile<T_REV><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_SENS: k_tile<T_SENS><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
-    case T_TRTRI: return launch_trtri_group(g, s);
+    case T_TRTRI:  // the inverse of a given factor: the cluster kernel without its factorisation
+    case T_POTRF: return launch_potrf_cluster_group(g, s);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

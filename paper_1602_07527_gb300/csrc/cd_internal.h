@@ -63,7 +63,10 @@ struct TileGroup {
   TileDesc d[kMaxTile];
 };
 
-enum TileOp { T_POTF2 = 0, T_REV = 1, T_SENS = 2, T_TRTRI = 3 };
+// T_POTRF: the diagonal tile on a cluster of CTAs.  X != null: factorise the
+// tile X in place (info as T_POTF2) and, if inv != null, write the inverse of
+// the factor; X == null: write the inverse of the given factor L.
+enum TileOp { T_POTF2 = 0, T_REV = 1, T_SENS = 2, T_TRTRI = 3, T_POTRF = 4 };
 
 // Grouped 2-D copies (one launch for the panels of every problem of a step).
 struct CopyDesc {
