@@ -329,12 +329,11 @@ struct TileBatch {
   }
   void flush() {
     if (g.count == 0) return;
-    static const char *names[5] = {"tile_potf2", "tile_rev", "tile_sens", "tile_trtri_cluster", "tile_potrf_cluster"};
+    static const char *names[5] = {"", "tile_rev", "tile_sens", "tile_trtri_cluster", "tile_potrf_cluster"};
     double flops = 0, bytes = 0;
     for (int p = 0; p < g.count; ++p) {
       const double t = g.d[p].t, tri = 0.5 * t * (t + 1) * 8.0;
       switch (op) {
-        case T_POTF2: flops += t * t * t / 3.0 * (g.d[p].inv ? 2.0 : 1.0); bytes += 2 * tri + (g.d[p].inv ? 8 * t * t : 0); break;
         case T_REV: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
         case T_SENS: flops += 2.0 * t * t * t / 3.0; bytes += 3 * tri; break;
         case T_TRTRI: flops += t * t * t / 3.0; bytes += tri + 8 * t * t; break;

@@ -1,7 +1,8 @@
 // FP64 kernels of libcholdiff: the grouped DFMA tile GEMM used for every
-// off-diagonal block update of the blocked algorithms (Sec. 4.2), and the
-// one-CTA diagonal-tile kernels that run the level-2 routines of Sec. 4.1 on
-// a tile held in shared memory.
+// off-diagonal block update of the blocked algorithms (Sec. 4.2), the
+// one-CTA diagonal-tile kernels that run the level-2 derivative routines of
+// Sec. 4.1 on a tile held in shared memory, and the diagonal-tile
+// factorisation and inverse on a thread-block cluster.
 //
 // On GB300 the FP64 pipe issues about two DFMA per clock per SM (measured:
 // 1.19 TFLOP/s for the whole GPU, 8 GFLOP/s on one SM), and DMMA
@@ -238,60 +239,6 @@ __device__ __forceinline__ int tri_row(int e) {
   return r;
 }
 
-// chol_unblocked (Sec. 4.1) on the tile, in right-looking order (the same
-// arithmetic as the paper's column loop, with each column's update applied
-// as soon as the column is final).  Per column: one thread forms the pivot's
-// square root and reciprocal; all threads scale the column by it; then the
-// rank-1 update of the trailing triangle is spread flat over all threads,
-// one FMA per element, so every warp is full.  cj holds the unscaled column
-// (double-buffered: the update writes the next column's values into cn).
-// Returns the first 0-based column whose pivot is not positive (or NaN), else -1.
-__device__ int dev_potf2(double *T, int t, double *cbuf, double *red) {
-  const int tid = threadIdx.x;
-  double *sc = cbuf + 2 * kTileMax;  // scaled column j
-  // flat index -> (row, column) of a trailing triangle, the same for every column
-  short2 *rc = reinterpret_cast<short2 *>(cbuf + 3 * kTileMax);
-  const int Emax = t * (t - 1) / 2;
-  for (int e = tid; e < Emax; e += blockDim.x) {
-    const int r = tri_row(e);
-    rc[e] = make_short2((short)r, (short)(e - r * (r + 1) / 2));
-  }
-  for (int i = tid; i < t; i += blockDim.x) cbuf[i] = T[pk(i, 0)];
-  __syncthreads();
-  for (int j = 0; j < t; ++j) {
-    double *cj = cbuf + (j & 1) * kTileMax;
-    double *cn = cbuf + ((j + 1) & 1) * kTileMax;
-    if (tid == 0) {
-      const double piv = cj[j];
-      const bool ok = piv > 0.0;
-      const double dj = ok ? sqrt(piv) : 0.0;
-      red[0] = ok ? 1.0 / dj : 0.0;
-      red[1] = ok ? 1.0 : 0.0;
-      T[pk(j, j)] = ok ? dj : piv;
-    }
-    __syncthreads();
-    if (red[1] == 0.0) return j;
-    const double rd = red[0];
-    for (int i = j + 1 + tid; i < t; i += blockDim.x) {
-      const double v = cj[i] * rd;
-      sc[i] = v;
-      T[pk(i, j)] = v;
-    }
-    __syncthreads();
-    const int m = t - j - 1;
-    const int E = m * (m + 1) / 2;
-    for (int e = tid; e < E; e += blockDim.x) {
-      const short2 q = rc[e];
-      const int cc = q.y, i = j + 1 + q.x, k = j + 1 + cc;
-      const double v = fma(-sc[i], sc[k], T[pk(i, k)]);
-      T[pk(i, k)] = v;
-      if (cc == 0) cn[i] = v;
-    }
-    __syncthreads();
-  }
-  return -1;
-}
-
 // chol_unblocked_rev (Sec. 4.1) on the tile: column j from t-1 down to 0,
 //   d_bar <- (d_bar - c^T c_bar / d) / d,  c_bar <- c_bar / d,
 //   r_bar <- r_bar - d_bar r - c_bar^T B,  B_bar <- B_bar - c_bar r,
@@ -374,72 +321,15 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
   if (t <= 0 || t > kTileMax) return;
   double *S0 = sm;
   double *S1 = sm + (kTileMax * (kTileMax + 1) / 2);
-  if (OP == T_POTF2) {
-    if (d.info != nullptr && *(volatile int *)d.info != 0) return;  // an earlier column failed
-    tile_load(S0, d.X, d.ldx, t);
-    __syncthreads();
-    const int bad = dev_potf2(S0, t, S1, red);
-    __syncthreads();
-    tile_store(S0, d.X, d.ldx, t);
-    if (bad >= 0 && threadIdx.x == 0 && d.info != nullptr) *d.info = d.col0 + bad + 1;
-  } else {
-    tile_load(S0, d.L, d.ldl, t);
-    tile_load(S1, d.X, d.ldx, t);
-    __syncthreads();
-    if (OP == T_REV)
-      dev_rev(S0, S1, t, red);
-    else
-      dev_sens(S0, S1, t);
-    __syncthreads();
-    tile_store(S1, d.X, d.ldx, t);
-  }
-}
-
-// X = T^{-1} for a lower tile T (t <= 128): every column of X is an
-// independent forward substitution T x = e_c, so each warp computes one
-// column (lanes split the dot products, a shuffle tree sums them) and a tile
-// spreads over t / 8 CTAs.  Writes the full t x t inverse, zeros above.
-constexpr int kInvCols = 8;  // columns (warps) per CTA
-constexpr size_t kInvSmem = sizeof(double) * (kTileMax * (kTileMax + 1) / 2 + kTileMax + kInvCols * kTileMax);
-
-__global__ void __launch_bounds__(32 * kInvCols) k_trtri_cols(const __grid_constant__ TileGroup g) {
-  extern __shared__ double sm[];
-  const TileDesc &d = g.d[blockIdx.y];
-  const int t = d.t;
-  const int c0 = blockIdx.x * kInvCols;
-  if (t <= 0 || t > kTileMax || c0 >= t) return;
-  double *S = sm;                                       // packed tile
-  double *rdiag = sm + kTileMax * (kTileMax + 1) / 2;   // 1 / T_ii
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double *x = rdiag + kTileMax + warp * kTileMax;       // this warp's column
-  tile_load(S, d.L, d.ldl, t);
+  tile_load(S0, d.L, d.ldl, t);
+  tile_load(S1, d.X, d.ldx, t);
   __syncthreads();
-  for (int i = threadIdx.x; i < t; i += blockDim.x) rdiag[i] = 1.0 / S[pk(i, i)];
+  if (OP == T_REV)
+    dev_rev(S0, S1, t, red);
+  else
+    dev_sens(S0, S1, t);
   __syncthreads();
-  const int c = c0 + warp;
-  if (c < t) {
-    for (int i = lane; i < c; i += 32) x[i] = 0.0;
-    if (lane == 0) x[c] = rdiag[c];
-    __syncwarp();
-    for (int i = c + 1; i < t; ++i) {
-      double s0 = 0.0;
-      for (int k = c + lane; k < i; k += 32) s0 = fma(S[pk(i, k)], x[k], s0);
-      s0 = warp_sum(s0);
-      if (lane == 0) x[i] = -s0 * rdiag[i];
-      __syncwarp();
-    }
-    for (int i = lane; i < t; i += 32) d.inv[(long long)i * d.ldinv + c] = x[i];
-  }
-}
-
-cudaError_t launch_trtri_group(const TileGroup &g, cudaStream_t s) {
-  if (g.count <= 0) return cudaSuccess;
-  int tmax = 0;
-  for (int p = 0; p < g.count; ++p) tmax = std::max(tmax, g.d[p].t);
-  if (tmax <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((tmax + kInvCols - 1) / kInvCols), (unsigned)g.count);
-  k_trtri_cols<<<grid, 32 * kInvCols, kInvSmem, s>>>(g);
-  return cudaGetLastError();
+  tile_store(S1, d.X, d.ldx, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -701,13 +591,10 @@ cudaError_t launch_potrf_cluster_group(const TileGroup &g, cudaStream_t s) {
 
 cudaError_t tile_kernels_init() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_tile<T_POTF2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
-    return e;
   if ((e = cudaFuncSetAttribute(k_tile<T_REV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;
   if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem))) return e;
   if ((e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem)))
     return e;
   return cudaSuccess;
@@ -716,7 +603,6 @@ cudaError_t tile_kernels_init() {
 cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
   if (g.count <= 0) return cudaSuccess;
   switch (op) {
-    case T_POTF2: k_tile<T_POTF2><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_REV: k_tile<T_REV><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_SENS: k_tile<T_SENS><<<g.count, kTileThreads, kTileSmem, s>>>(g); break;
     case T_TRTRI:  // the inverse of a given factor: the cluster kernel without its factorisation

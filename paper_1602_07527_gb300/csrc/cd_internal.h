@@ -63,10 +63,12 @@ struct TileGroup {
   TileDesc d[kMaxTile];
 };
 
-// T_POTRF: the diagonal tile on a cluster of CTAs.  X != null: factorise the
-// tile X in place (info as T_POTF2) and, if inv != null, write the inverse of
-// the factor; X == null: write the inverse of the given factor L.
-enum TileOp { T_POTF2 = 0, T_REV = 1, T_SENS = 2, T_TRTRI = 3, T_POTRF = 4 };
+// T_REV / T_SENS: the level-2 derivative loops on one CTA.  T_POTRF: the
+// diagonal tile on a cluster of CTAs: factorise X in place (info set at the
+// first non-positive pivot) and, if inv != null, write the inverse of the
+// factor.  T_TRTRI: the same kernel writing only the inverse of the given
+// factor L.
+enum TileOp { T_REV = 1, T_SENS = 2, T_TRTRI = 3, T_POTRF = 4 };
 
 // Grouped 2-D copies (one launch for the panels of every problem of a step).
 struct CopyDesc {
