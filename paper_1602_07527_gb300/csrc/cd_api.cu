@@ -188,6 +188,14 @@ struct Ctx {
     cuda(cudaEventRecord(h->ev_join, side));
     cuda(cudaStreamWaitEvent(s, h->ev_join, 0));
   }
+  // mark(): a point in the side stream's work so far; wait_mark(): s waits
+  // for that point only (the side stream's later work may still run).
+  void mark() {
+    if (side) cuda(cudaEventRecord(h->ev_mid, side));
+  }
+  void wait_mark() {
+    if (side) cuda(cudaStreamWaitEvent(s, h->ev_mid, 0));
+  }
 };
 
 const char *kAName[6] = {"N", "T", "SYM2", "TL", "SYM1", "NL"};
@@ -267,6 +275,9 @@ struct GemmBatch {
     sub.bmode = g.bmode;
     sub.lower = g.lower;
     sub.phi = g.phi;
+    sub.tri = g.tri;
+    const int ntri = ((g.tri & (TRI_A_UPPER | TRI_A_LOWER)) ? 1 : 0) + ((g.tri & (TRI_B_LOWER | TRI_B_UPPER)) ? 1 : 0);
+    const double tri_frac = ntri == 0 ? 1.0 : (ntri == 1 ? 0.5 : 1.0 / 3.0);  // nonzero share of the K terms
     size_t used = 0;
     double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
@@ -303,7 +314,7 @@ struct GemmBatch {
       sub.total_tiles += per_split(d) * sp;
       sub.d[sub.count++] = d;
       const double outs = g.lower ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N;
-      flops += 2.0 * d.K * outs;
+      flops += 2.0 * d.K * outs * tri_frac;
       bytes += 8.0 * ((double)d.M * d.K + (double)d.K * d.N + outs * (d.beta != 0.0 ? 2.0 : 1.0));
       if (sp > 1) {
         red = true;
@@ -405,15 +416,18 @@ void rev_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
   {  // P = Phi(D^T D_bar)
     GemmBatch gb(c, A_TL, B_NL, true);
     gb.g.phi = 1;
+    gb.g.tri = TRI_A_UPPER | TRI_B_LOWER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.D, x.ldd, x.Db, x.lddb, nullptr, 0, x.T1, x.ldt, 1.0, 0.0);
   }
-  {  // Y = (P + P^T) D^{-1}
+  {  // Y = (P + P^T) D^{-1}   (D^{-1} lower)
     GemmBatch gb(c, A_SYM2, B_N, false);
+    gb.g.tri = TRI_B_LOWER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.T1, x.ldt, x.Dinv, x.ldt, nullptr, 0, x.T2, x.ldt, 1.0, 0.0);
   }
-  {  // D_bar = Phi(D^{-T} Y)
+  {  // D_bar = Phi(D^{-T} Y)   (D^{-T} upper)
     GemmBatch gb(c, A_T, B_N, true);
     gb.g.phi = 1;
+    gb.g.tri = TRI_A_UPPER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.Dinv, x.ldt, x.T2, x.ldt, nullptr, 0, x.Db, x.lddb, 1.0, 0.0);
   }
 }
@@ -422,17 +436,20 @@ void rev_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
 // D_dot <- D Phi(D^{-1} S D^{-T}), S the symmetric block whose lower triangle
 // is D_dot.
 void sens_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
-  {  // Z = S D^{-T}
+  {  // Z = S D^{-T}   (D^{-T} upper)
     GemmBatch gb(c, A_SYM1, B_T, false);
+    gb.g.tri = TRI_B_UPPER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.Db, x.lddb, x.Dinv, x.ldt, nullptr, 0, x.T1, x.ldt, 1.0, 0.0);
   }
-  {  // X = Phi(D^{-1} Z)
+  {  // X = Phi(D^{-1} Z)   (D^{-1} lower)
     GemmBatch gb(c, A_N, B_N, true);
     gb.g.phi = 1;
+    gb.g.tri = TRI_A_LOWER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.Dinv, x.ldt, x.T1, x.ldt, nullptr, 0, x.T2, x.ldt, 1.0, 0.0);
   }
-  {  // D_dot = D X
+  {  // D_dot = D X   (both lower)
     GemmBatch gb(c, A_NL, B_NL, true);
+    gb.g.tri = TRI_A_LOWER | TRI_B_LOWER;
     for (auto &x : v) gb.add(x.w, x.w, x.w, x.D, x.ldd, x.T2, x.ldt, nullptr, 0, x.Db, x.lddb, 1.0, 0.0);
   }
 }
@@ -460,10 +477,12 @@ void trtri_big(Ctx &c, const double *D, long long ldd, double *inv, long long ld
   if (!T) { c.err = CD_ENOMEM; return; }
   {
     GemmBatch gb(c, A_N, B_N, false);  // T = D21 inv11
+    gb.g.tri = TRI_B_LOWER;
     gb.add(h2, h1, h1, D + (long long)h1 * ldd, ldd, inv, ldinv, nullptr, 0, T, h1, 1.0, 0.0);
   }
   {
     GemmBatch gb(c, A_N, B_N, false);  // inv21 = -inv22 T  (inv22 lower, zero above)
+    gb.g.tri = TRI_A_LOWER;
     gb.add(h2, h1, h2, inv + (long long)h1 * ldinv + h1, ldinv, T, h1, nullptr, 0, inv + (long long)h1 * ldinv,
            ldinv, -1.0, 0.0);
   }
@@ -521,6 +540,7 @@ void precompute_dinv(Ctx &c, std::vector<Prob> &P, int nb, bool rev_partition, A
   // top-right quarter of its own nb x nb inverse buffer, cleared afterwards.
   {
     GemmBatch gb(c, A_N, B_N, false);
+    gb.g.tri = TRI_B_LOWER;
     for (auto &b : two) {
       const int h1 = (b.w / 2 + 63) / 64 * 64, h2 = b.w - h1;
       gb.add(h2, h1, h1, b.D + (long long)h1 * b.ldd, b.ldd, b.inv, nb, nullptr, 0, b.inv + h1, nb, 1.0, 0.0);
@@ -528,6 +548,7 @@ void precompute_dinv(Ctx &c, std::vector<Prob> &P, int nb, bool rev_partition, A
   }
   {
     GemmBatch gb(c, A_N, B_N, false);
+    gb.g.tri = TRI_A_LOWER;
     for (auto &b : two) {
       const int h1 = (b.w / 2 + 63) / 64 * 64, h2 = b.w - h1;
       gb.add(h2, h1, h2, b.inv + (long long)h1 * nb + h1, nb, b.inv + h1, nb, nullptr, 0, b.inv + (long long)h1 * nb,
@@ -612,6 +633,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     c.join();
     {  // f4: C <- C tril(D)^{-T}   (W = C Dinv^T, then copy back)
       GemmBatch gb(c, A_N, B_T, false);
+      gb.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -645,6 +667,7 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     {  // r1: C_bar <- C_bar D^{-1}   (into W)
       GemmBatch gb(c, A_N, B_N, false);
+      gb.g.tri = TRI_B_LOWER;
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -802,6 +825,7 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     c.join();
     {  // g4a: C_dot <- C_dot - C D_dot^T
       GemmBatch gb(c, A_N, B_TL, false);
+      gb.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -813,6 +837,7 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     {  // g4b: C_dot <- C_dot D^{-T}   (into W, then copy back)
       GemmBatch gb(c, A_N, B_T, false);
+      gb.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
@@ -945,6 +970,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     c.join();
     {  // f4: W = C D^{-T}, the finished panel of L
       GemmBatch gb(c, A_N, B_T, false);
+      gb.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -954,6 +980,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     {  // g4: W2 = (C_dot - W D_dot^T) D^{-T}, the finished panel of L_dot
       GemmBatch ga(c, A_N, B_TL, false);
+      ga.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -963,6 +990,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
       ga.flush();
       GemmBatch gb(c, A_N, B_T, false);
+      gb.g.tri = TRI_B_UPPER;
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
@@ -1098,7 +1126,9 @@ struct MixedBatch {
     snprintf(name, sizeof(name), "mgemm_bf16x%d%s%s%s", prods, lower ? "_tril" : "", tag ? " " : "", tag ? tag : "");
     c.launch(name, flops, bytes, st, [&] {
       int l = 0;
-      cudaError_t err = mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l);
+      const bool bulk = c.side && st == c.side;
+      cudaError_t err = mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l, 0,
+                                          bulk ? kUnitsPerCtaBulk : kUnitsPerCtaChain);
       if (l > 1) c.h->launches += l - 1;
       return err;
     });
@@ -1230,6 +1260,19 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     c.fork();
+    {  // r5, first part (side stream): R_bar <- R_bar - C_bar^T B.  It needs
+       // neither r3 nor r4, so it leaves the diagonal chain.
+      MixedBatch mb(c, T, false, true, "r5a");
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k) || j == 0) continue;
+        const int w = k - j, m = p.n - k;
+        double *Rb = p.X + (long long)j * p.ldx;
+        mb.add(mop(p.mx.P2, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, k + p.mx.pad, 0), w, j, m, Rb,
+               p.ldx, Rb, p.ldx, -1.0, 1.0);
+      }
+    }
+    c.mark();  // r5's second part waits for this point only
     {  // r2 (side stream): B_bar <- B_bar - C_bar R
       MixedBatch mb(c, T, false, true, "r2");
       for (auto &p : P) {
@@ -1283,25 +1326,26 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         }
       }
     }
-    {  // r5: R_bar <- R_bar - G L[j:n, 0:j],  G = [D_bar + D_bar^T, C_bar^T]
+    {  // r5, second part: R_bar <- R_bar - (D_bar + D_bar^T) R, after r4 and the first part
       {
         SplitBatch sb(c);
         for (auto &p : P) {
           int j, k;
           if (!blk(p, s, j, k) || j == 0) continue;
           const int w = k - j;
-          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, p.n - j, 2, 0, p.mx.P3, p.mx.ldn, nb, 0, 0, w,
-                (int)p.mx.ldn, 0, 0, T);
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, w, 2, 0, p.mx.P3, p.mx.ldn, nb, 0, 0, w,
+                (w + 63) / 64 * 64, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false, false, "r5");
+      c.wait_mark();
+      MixedBatch mb(c, T, false, false, "r5b");
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k) || j == 0) continue;
         const int w = k - j;
         double *Rb = p.X + (long long)j * p.ldx;
-        mb.add(mop(p.mx.P3, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), w, j, p.n - j,
-               Rb, p.ldx, Rb, p.ldx, -1.0, 1.0);
+        mb.add(mop(p.mx.P3, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), w, j, w, Rb,
+               p.ldx, Rb, p.ldx, -1.0, 1.0);
       }
     }
     c.join();
@@ -1955,7 +1999,8 @@ int cd_create(cd_handle **h, int device) {
       cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_mid, cudaEventDisableTiming) != cudaSuccess) {
     cudaFree(x->dev_err);
     free(x);
     return CD_ECUDA;
@@ -1976,6 +2021,7 @@ int cd_destroy(cd_handle *h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_mid) cudaEventDestroy(h->ev_mid);
   free(h);
   return CD_OK;
 }

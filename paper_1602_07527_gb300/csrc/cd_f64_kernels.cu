@@ -71,6 +71,13 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
   }
   const int kbeg = z * d.kchunk;
   const int kend = min(d.K, kbeg + d.kchunk);
+  // K range of this tile: triangular operands are zero outside [klo, khi)
+  int klo = kbeg, khi = kend;
+  if (g.tri & TRI_A_UPPER) klo = max(klo, m0);
+  if (g.tri & TRI_B_LOWER) klo = max(klo, n0);
+  if (g.tri & TRI_A_LOWER) khi = min(khi, m0 + GBM);
+  if (g.tri & TRI_B_UPPER) khi = min(khi, n0 + GBN);
+  const int kfirst = kbeg + (klo - kbeg) / GBK * GBK;  // K blocks stay aligned to the split's start
   const double *__restrict__ A = d.A;
   const double *__restrict__ B = d.B;
   const long long lda = d.lda, ldb = d.ldb;
@@ -84,14 +91,14 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+  for (int k0 = kfirst; k0 < khi; k0 += GBK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int e = tid + r * GT;
       int kk, ii;
       if (AM == A_T) { ii = e & 63; kk = e >> 6; } else { kk = e & 15; ii = e >> 4; }
       const int gi = m0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < M && gk < kend) ? load_a<AM>(A, lda, gi, gk) : 0.0;
+      As[kk][ii] = (gi < M && gk < khi) ? load_a<AM>(A, lda, gi, gk) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
       int kk, jj;
       if (BM == B_N) { jj = e & 63; kk = e >> 6; } else { kk = e & 15; jj = e >> 4; }
       const int gj = n0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < kend) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
+      Bs[kk][jj] = (gj < N && gk < khi) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
     }
     __syncthreads();
 #pragma unroll

@@ -36,12 +36,23 @@ struct GemmDesc {
   int tiles_m, tiles_n, tile_begin, kchunk;
 };
 
+// Triangular operands (GemmGroup::tri): a product term a(i,k) b(k,j) known to
+// be zero over part of K lets each output tile skip those K blocks exactly.
+enum TriMask {
+  TRI_A_UPPER = 1,  // a(i,k) = 0 for k < i
+  TRI_A_LOWER = 2,  // a(i,k) = 0 for k > i
+  TRI_B_LOWER = 4,  // b(k,j) = 0 for k < j
+  TRI_B_UPPER = 8   // b(k,j) = 0 for k > j
+};
+
 constexpr int kMaxGemm = 32;
 struct GemmGroup {
   int count, total_tiles;
   int amode, bmode, lower, phi;  // phi: halve the diagonal of a lower output (Eq. phi)
+  int tri;                       // TriMask bits (0: general operands)
   GemmDesc d[kMaxGemm];
 };
+static_assert(sizeof(GemmGroup) <= 4096, "kernel parameter block too large");
 
 // ---------------------------------------------------------------------------
 // One-CTA diagonal-tile kernels (t <= kTileMax, tile in shared memory).
@@ -104,6 +115,7 @@ struct cd_handle {
   cudaStream_t side;           // second stream for work independent of the diagonal chain
   cudaStream_t crit;           // high-priority stream for the diagonal (critical) chain
   cudaEvent_t ev_fork, ev_join, ev_in, ev_out;
+  cudaEvent_t ev_mid;          // a point inside the side stream's work of a step
 };
 
 namespace cd {

@@ -703,10 +703,6 @@ bool encode_map(CUtensorMap *m, const MOp &op) {
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Units per CTA at most: a persistent CTA holds its SM until its last unit,
-// so a long product launched on the bulk stream must still hand SMs back
-// every few tiles to the diagonal chain's launches on the high-priority stream.
-constexpr int kMaxUnitsPerCta = 4;
 
 int sm_count() {
   static int cached[64];
@@ -721,9 +717,9 @@ int sm_count() {
 }
 
 template <int T, bool LOWER>
-cudaError_t launch_one(const MGroup &g, cudaStream_t s) {
+cudaError_t launch_one(const MGroup &g, cudaStream_t s, int max_units) {
   const int units = g.total_tiles;
-  const int grid = std::min(units, std::max(sm_count(), (units + kMaxUnitsPerCta - 1) / kMaxUnitsPerCta));
+  const int grid = std::min(units, std::max(sm_count(), (units + max_units - 1) / max_units));
   k_mgemm<T, LOWER><<<grid, kThreads, dyn_smem<T>(), s>>>(g);
   return cudaGetLastError();
 }
@@ -769,7 +765,8 @@ size_t mixed_workspace_bytes(int n, int nb, int prec) {
 }
 
 cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
-                              int *launches, int tx_extra) {
+                              int *launches, int tx_extra, int max_units) {
+  max_units = std::max(1, max_units);
   if (T != 2 && T != 3) return cudaErrorInvalidValue;
   int i = 0;
   while (i < count) {
@@ -823,9 +820,9 @@ cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lowe
     if (g.count == 0) continue;
     cudaError_t e;
     if (T == 2)
-      e = lower ? launch_one<2, true>(g, s) : launch_one<2, false>(g, s);
+      e = lower ? launch_one<2, true>(g, s, max_units) : launch_one<2, false>(g, s, max_units);
     else
-      e = lower ? launch_one<3, true>(g, s) : launch_one<3, false>(g, s);
+      e = lower ? launch_one<3, true>(g, s, max_units) : launch_one<3, false>(g, s, max_units);
     if (launches) ++*launches;
     if (e != cudaSuccess) return e;
     if (any_split) {

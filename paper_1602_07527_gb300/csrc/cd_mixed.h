@@ -53,8 +53,13 @@ int mixed_ctas_per_sm();                                // resident GEMM CTAs pe
 // tx_extra is a test hook (0 in production): the first load barrier of each
 // CTA expects that many bytes more than its copy delivers, so the bounded
 // wait of the MMA thread runs out and the kernel reports CD_ETIMEOUT.
+// max_units bounds the output tiles one persistent CTA takes: a CTA holds its
+// SM until its last tile, so products on the bulk stream take few tiles per
+// CTA and hand SMs back to the diagonal chain's launches.
+constexpr int kUnitsPerCtaChain = 4;
+constexpr int kUnitsPerCtaBulk = 4;
 cudaError_t mixed_gemm_launch(const MProblem *probs, int count, int T, bool lower, int *dev_err, cudaStream_t s,
-                              int *launches, int tx_extra = 0);
+                              int *launches, int tx_extra = 0, int max_units = kUnitsPerCtaChain);
 
 // Split an FP64 view into T BF16 term arrays (see MOp).  The view is
 // rows x cols of src (lower-triangle mode 1 keeps r >= c; mode 2 is the
