@@ -1017,6 +1017,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // Phi / halving steps stay in FP64 (the kernels above).
 // ============================================================================
 constexpr int kMixMaxChunk = 2048;  // longest FP32 accumulation before an FP64 reduction
+constexpr int kMixMinKbPerSplit = 8;  // shortest K range (64-wide blocks) of one split-K part
 
 MOp mop(void *base, long long ld, long long rows, int T, int x0, int y0) {
   MOp o;
@@ -1111,8 +1112,11 @@ struct MixedBatch {
     const int kblocks = (P.K + 63) / 64;
     int sg = 1;
     if (t1 < 4LL * slots) {
+      // each split keeps at least kMixMinKbPerSplit K blocks: a CTA's fixed
+      // cost and the FP32 partial traffic outweigh finer parallelism
+      const int smax = std::min(64, std::max(1, kblocks / kMixMinKbPerSplit));
       double best = wave_eff(t1, slots);
-      for (int s2 = 2; s2 <= std::min(kblocks, 64) && best < 0.9; ++s2) {
+      for (int s2 = 2; s2 <= smax && best < 0.9; ++s2) {
         const double e = wave_eff(t1 * s2, slots);
         if (e > best + 0.02) { sg = s2; best = e; }
       }
