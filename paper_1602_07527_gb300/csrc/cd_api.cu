@@ -198,6 +198,9 @@ struct Ctx {
   }
 };
 
+// Products of at most this many multiply-adds use 32 x 32 output tiles.
+constexpr double kSmallGemmWork = 67108864.0;
+
 const char *kAName[6] = {"N", "T", "SYM2", "TL", "SYM1", "NL"};
 const char *kBName[4] = {"N", "T", "TL", "NL"};
 
@@ -236,14 +239,20 @@ struct GemmBatch {
     d.part = nullptr;
   }
   int per_split(const GemmDesc &d) const { return g.lower ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n; }
+  // Output tile size of one problem, from its own shape: small products use
+  // 32 x 32 tiles so that their work spreads over every SM's FP64 unit.
+  int tile_size(const GemmDesc &d) const {
+    const double outs = g.lower ? 0.5 * d.M * (d.M + 1.0) : (double)d.M * d.N;
+    return outs * d.K <= kSmallGemmWork ? 32 : 64;
+  }
   static double wave_eff(long long ctas, int slots) {
     const long long waves = (ctas + slots - 1) / slots;
     return (double)ctas / (double)(waves * slots);
   }
   // Split-K factor of one problem from its own shape only, so that a
   // problem gets the same arithmetic whether it runs alone or in a batch.
-  int choose_splits(const GemmDesc &d) const {
-    const int slots = std::max(1, c.target_ctas);
+  int choose_splits(const GemmDesc &d, int ts) const {
+    const int slots = std::max(1, ts == 32 ? c.h->gemm_slots_small : c.target_ctas);
     const long long t1 = per_split(d);
     if (t1 >= 4LL * slots || d.K < 32) return 1;
     const int smax = std::min(64, d.K / 16);
@@ -262,13 +271,13 @@ struct GemmBatch {
   void launch_sub(GemmGroup &sub, bool red, double flops, double bytes, double rbytes) {
     if (sub.count == 0) return;
     char name[48];
-    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "",
-             g.phi ? "_phi" : "");
+    snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s%s%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "",
+             g.phi ? "_phi" : "", sub.ts == 32 ? "_t32" : "");
     c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(sub, st); });
     if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
   }
-  void flush() {
-    if (g.count == 0) return;
+  // One launch (or more, if the partial region fills) per tile size.
+  void flush_ts(int ts) {
     GemmGroup sub;
     memset(&sub, 0, sizeof(sub));
     sub.amode = g.amode;
@@ -276,6 +285,7 @@ struct GemmBatch {
     sub.lower = g.lower;
     sub.phi = g.phi;
     sub.tri = g.tri;
+    sub.ts = ts;
     const int ntri = ((g.tri & (TRI_A_UPPER | TRI_A_LOWER)) ? 1 : 0) + ((g.tri & (TRI_B_LOWER | TRI_B_UPPER)) ? 1 : 0);
     const double tri_frac = ntri == 0 ? 1.0 : (ntri == 1 ? 0.5 : 1.0 / 3.0);  // nonzero share of the K terms
     size_t used = 0;
@@ -283,7 +293,10 @@ struct GemmBatch {
     bool red = false;
     for (int p = 0; p < g.count; ++p) {
       GemmDesc d = g.d[p];
-      int sp = std::min(choose_splits(d), std::max(1, d.K / 16));
+      if (tile_size(d) != ts) continue;
+      d.tiles_m = (d.M + ts - 1) / ts;
+      d.tiles_n = (d.N + ts - 1) / ts;
+      int sp = std::min(choose_splits(d, ts), std::max(1, d.K / 16));
       int kchunk = std::max(d.K, 1);
       if (sp > 1) {
         kchunk = ((d.K + sp - 1) / sp + 15) / 16 * 16;
@@ -322,6 +335,11 @@ struct GemmBatch {
       }
     }
     launch_sub(sub, red, flops, bytes, rbytes);
+  }
+  void flush() {
+    if (g.count == 0) return;
+    flush_ts(64);
+    flush_ts(32);
     g.count = 0;
     g.total_tiles = 0;
   }
@@ -1928,6 +1946,8 @@ int rev_in_scratch(int n, const double *L, long long ldl, double *Abar, long lon
   memset(&hh, 0, sizeof(hh));
   cudaGetDevice(&hh.device);
   hh.num_sms = num_sms;
+  hh.gemm_slots = 2 * num_sms;
+  hh.gemm_slots_small = gemm_ctas_per_sm(32) * num_sms;  // an occupancy query: no allocation
   Arena ar;
   ar.base = (char *)scratch;
   ar.cap = scratch_bytes;
@@ -1939,7 +1959,7 @@ int rev_in_scratch(int n, const double *L, long long ldl, double *Abar, long lon
   std::vector<Prob> P(1);
   P[0] = Prob{n, L, ldl, Abar, lda, nullptr, nullptr, nullptr, 0};
   if (!bind_workspace(P, nb, ar)) return CD_EINVAL;
-  Ctx c{&hh, s, &opt, nullptr, 0, 2 * num_sms};
+  Ctx c{&hh, s, &opt, nullptr, 0, hh.gemm_slots};
   const size_t left = ar.cap > align_up(ar.off) ? ar.cap - align_up(ar.off) : 0;
   c.part_cap = left / sizeof(double);
   c.part = c.part_cap ? (double *)ar.take(c.part_cap * sizeof(double)) : nullptr;
@@ -1995,7 +2015,8 @@ int cd_create(cd_handle **h, int device) {
     free(x);
     return CD_ECUDA;
   }
-  x->gemm_slots = gemm_ctas_per_sm() * x->num_sms;
+  x->gemm_slots = gemm_ctas_per_sm(64) * x->num_sms;
+  x->gemm_slots_small = gemm_ctas_per_sm(32) * x->num_sms;
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&x->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||

@@ -21,7 +21,7 @@ namespace cd {
 // ---------------------------------------------------------------------------
 // Grouped GEMM
 // ---------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 16, GT = 256;
+constexpr int GBK = 16;
 
 template <int AM>
 __device__ __forceinline__ double load_a(const double *__restrict__ A, long long lda, int i, int k) {
@@ -43,11 +43,15 @@ __device__ __forceinline__ double load_b(const double *__restrict__ B, long long
   return (j >= k) ? B[(long long)j * ldb + k] : 0.0;
 }
 
-// One CTA computes a 64 x 64 output tile over its K range; each thread owns a
-// 4 x 4 micro-tile (rows ty + 16 r, columns tx + 16 c), so a warp reads two
-// A values (broadcast) and sixteen consecutive B values per k.
-template <int AM, int BM, bool LOWER>
-__global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGroup g) {
+// One CTA computes a TS x TS output tile over its K range; each thread owns a
+// 4 x 4 micro-tile (rows ty + TS/4 r, columns tx + TS/4 c), so a warp reads
+// few A values (broadcast) and consecutive B values per k.  TS = 64 (256
+// threads) for ordinary products; TS = 32 (64 threads) for small ones, where
+// a 64 x 64 x 16 chunk alone would hold one SM's FP64 unit for ~16 us and too
+// few CTAs would share the product's work.
+template <int AM, int BM, bool LOWER, int TS>
+__global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant__ GemmGroup g) {
+  constexpr int TD = TS / 4, NT = TD * TD, LOADS = GBK * TS / NT;
   const int bid = blockIdx.x;
   int p = 0;
   while (p + 1 < g.count && bid >= g.d[p + 1].tile_begin) ++p;
@@ -63,11 +67,11 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
     int ti = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
     while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
     while (ti * (ti + 1) / 2 > rem) --ti;
-    m0 = ti * GBM;
-    n0 = (rem - ti * (ti + 1) / 2) * GBN;
+    m0 = ti * TS;
+    n0 = (rem - ti * (ti + 1) / 2) * TS;
   } else {
-    m0 = (rem / d.tiles_n) * GBM;
-    n0 = (rem % d.tiles_n) * GBN;
+    m0 = (rem / d.tiles_n) * TS;
+    n0 = (rem % d.tiles_n) * TS;
   }
   const int kbeg = z * d.kchunk;
   const int kend = min(d.K, kbeg + d.kchunk);
@@ -75,16 +79,16 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
   int klo = kbeg, khi = kend;
   if (g.tri & TRI_A_UPPER) klo = max(klo, m0);
   if (g.tri & TRI_B_LOWER) klo = max(klo, n0);
-  if (g.tri & TRI_A_LOWER) khi = min(khi, m0 + GBM);
-  if (g.tri & TRI_B_UPPER) khi = min(khi, n0 + GBN);
+  if (g.tri & TRI_A_LOWER) khi = min(khi, m0 + TS);
+  if (g.tri & TRI_B_UPPER) khi = min(khi, n0 + TS);
   const int kfirst = kbeg + (klo - kbeg) / GBK * GBK;  // K blocks stay aligned to the split's start
   const double *__restrict__ A = d.A;
   const double *__restrict__ B = d.B;
   const long long lda = d.lda, ldb = d.ldb;
 
-  __shared__ double As[GBK][GBM + 1];
-  __shared__ double Bs[GBK][GBN + 1];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __shared__ double As[GBK][TS + 1];
+  __shared__ double Bs[GBK][TS + 1];
+  const int tid = threadIdx.x, tx = tid % TD, ty = tid / TD;
   double acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -93,18 +97,18 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
 
   for (int k0 = kfirst; k0 < khi; k0 += GBK) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = tid + r * GT;
+    for (int r = 0; r < LOADS; ++r) {
+      const int e = tid + r * NT;
       int kk, ii;
-      if (AM == A_T) { ii = e & 63; kk = e >> 6; } else { kk = e & 15; ii = e >> 4; }
+      if (AM == A_T) { ii = e % TS; kk = e / TS; } else { kk = e % GBK; ii = e / GBK; }
       const int gi = m0 + ii, gk = k0 + kk;
       As[kk][ii] = (gi < M && gk < khi) ? load_a<AM>(A, lda, gi, gk) : 0.0;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = tid + r * GT;
+    for (int r = 0; r < LOADS; ++r) {
+      const int e = tid + r * NT;
       int kk, jj;
-      if (BM == B_N) { jj = e & 63; kk = e >> 6; } else { kk = e & 15; jj = e >> 4; }
+      if (BM == B_N) { jj = e % TS; kk = e / TS; } else { kk = e % GBK; jj = e / GBK; }
       const int gj = n0 + jj, gk = k0 + kk;
       Bs[kk][jj] = (gj < N && gk < khi) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
     }
@@ -113,9 +117,9 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
     for (int kk = 0; kk < GBK; ++kk) {
       double a[4], b[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TD * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TD * c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -127,11 +131,11 @@ __global__ void __launch_bounds__(GT) k_gemm_f64(const __grid_constant__ GemmGro
   const double alpha = d.alpha, beta = d.beta;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int i = m0 + ty + 16 * r;
+    const int i = m0 + ty + TD * r;
     if (i >= M) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int j = n0 + tx + 16 * c;
+      const int j = n0 + tx + TD * c;
       if (j >= N || (LOWER && j > i)) continue;
       if (d.splits == 1) {
         double v = alpha * acc[r][c];
@@ -165,10 +169,17 @@ __global__ void k_reduce_f64(const __grid_constant__ GemmGroup g) {
 
 template <int AM, int BM>
 static cudaError_t launch_gemm_ab(const GemmGroup &g, cudaStream_t s) {
-  if (g.lower)
-    k_gemm_f64<AM, BM, true><<<g.total_tiles, GT, 0, s>>>(g);
-  else
-    k_gemm_f64<AM, BM, false><<<g.total_tiles, GT, 0, s>>>(g);
+  if (g.ts == 32) {
+    if (g.lower)
+      k_gemm_f64<AM, BM, true, 32><<<g.total_tiles, 64, 0, s>>>(g);
+    else
+      k_gemm_f64<AM, BM, false, 32><<<g.total_tiles, 64, 0, s>>>(g);
+  } else {
+    if (g.lower)
+      k_gemm_f64<AM, BM, true, 64><<<g.total_tiles, 256, 0, s>>>(g);
+    else
+      k_gemm_f64<AM, BM, false, 64><<<g.total_tiles, 256, 0, s>>>(g);
+  }
   return cudaGetLastError();
 }
 
@@ -188,10 +199,17 @@ cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s) {
   }
 }
 
-int gemm_ctas_per_sm() {
+int gemm_ctas_per_sm(int ts) {
   int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false>, GT, 0) != cudaSuccess) a = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false>, GT, 0) != cudaSuccess) b = 1;
+  if (ts == 32) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 32>, 64, 0) != cudaSuccess) a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 32>, 64, 0) != cudaSuccess)
+      b = 1;
+  } else {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 64>, 256, 0) != cudaSuccess) a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 64>, 256, 0) != cudaSuccess)
+      b = 1;
+  }
   return std::max(1, std::min(a, b));
 }
 

@@ -50,6 +50,7 @@ struct GemmGroup {
   int count, total_tiles;
   int amode, bmode, lower, phi;  // phi: halve the diagonal of a lower output (Eq. phi)
   int tri;                       // TriMask bits (0: general operands)
+  int ts;                        // output tile size of the launch: 64, or 32 for small products
   GemmDesc d[kMaxGemm];
 };
 static_assert(sizeof(GemmGroup) <= 4096, "kernel parameter block too large");
@@ -111,7 +112,8 @@ struct cd_handle {
   long long launches;
   int prof_on;  // cd_profile_enable
   void *prof;   // profiler state (cd_api.cu)
-  int gemm_slots;              // resident FP64 GEMM CTAs on the whole GPU
+  int gemm_slots;              // resident FP64 GEMM CTAs on the whole GPU (64 x 64 tiles)
+  int gemm_slots_small;        // the same for 32 x 32 tiles
   cudaStream_t side;           // second stream for work independent of the diagonal chain
   cudaStream_t crit;           // high-priority stream for the diagonal (critical) chain
   cudaEvent_t ev_fork, ev_join, ev_in, ev_out;
@@ -128,5 +130,5 @@ cudaError_t launch_copy(const double *src, long long lds, double *dst, long long
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
 cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
-int gemm_ctas_per_sm();  // resident CTAs of the FP64 GEMM per SM
+int gemm_ctas_per_sm(int ts);  // resident CTAs of the FP64 GEMM per SM (tile size ts)
 }  // namespace cd
