@@ -194,6 +194,19 @@ int cd_chol_fwd_and_sens_batched(cd_handle *h, int batch, const int *n, double *
                                  const cd_options *opt, void *stream, int *info);
 
 /*
+ * Explicit Jacobian of the factor (Eq. delements), for analysis and testing:
+ *   J[((i n + j) n + k) n + l] = d L_ij / d Sigma_kl   for i >= j, k >= l,
+ * where Sigma_kl and Sigma_lk (k != l) are one tied input, as in Eq. symrev;
+ * every other entry is 0.  L (n x n, ldl, lower triangle read) is the factor;
+ * J is a caller-owned device array of n^4 doubles.  Theta(n^4) time and
+ * memory (n = 128 needs 2.1 GB): this is not the blocked hot path, whose
+ * Jacobian-vector products are cd_chol_fwd_sens and cd_chol_rev.  The
+ * handle's workspace holds L^{-1} and the n^3 partial sums of the formula.
+ * FP64 only.  Asynchronous on stream.
+ */
+int cd_chol_jacobian(cd_handle *h, int n, const double *L, long long ldl, double *J, void *stream);
+
+/*
  * Reverse mode without any allocation (no counterpart in the paper: this is a
  * service for callers, not a step of the method).
  *

@@ -2119,6 +2119,31 @@ int cd_chol_fwd_and_sens_batched(cd_handle *h, int batch, const int *n, double *
   return run(h, OP_DUAL, batch, n, nullptr, nullptr, A, lda, opt, stream, info, Adot, ldadot);
 }
 
+int cd_chol_jacobian(cd_handle *h, int n, const double *L, long long ldl, double *J, void *stream) {
+  if (!h || n < 0 || (n > 0 && (!L || !J || ldl < n))) return CD_EINVAL;
+  if (n == 0) return CD_OK;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t need = align_up(sizeof(double) * (size_t)n * n) + align_up(sizeof(double) * (size_t)n * n * n) +
+                      align_up(sizeof(double) * (size_t)n * n) + 8 * kAlign;  // L^{-1}, S, the inverse's scratch
+  int rc = ensure_ws(h, need, s);
+  if (rc) return rc;
+  Arena ar;
+  ar.base = (char *)h->ws;
+  ar.cap = h->ws_bytes;
+  cd_options opt;
+  cd_options_default(&opt);
+  Ctx c{h, s, &opt, nullptr, 0, h->gemm_slots};
+  double *Li = (double *)ar.take(sizeof(double) * (size_t)n * n);
+  double *S = (double *)ar.take(sizeof(double) * (size_t)n * n * n);
+  if (!Li || !S) return CD_ENOMEM;
+  trtri_big(c, L, ldl, Li, n, n, ar);  // L^{-1}, full storage, zeros above the diagonal
+  if (c.err) return c.err;
+  const double n4 = (double)n * n * n * n;
+  c.launch("jacobian", 4.0 * n4, 8.0 * n4, [&] { return launch_jacobian(n, L, ldl, Li, n, S, J, s); });
+  return c.err;
+}
+
 int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {
   if (!h) return CD_EINVAL;
   DeviceGuard guard(h->device);

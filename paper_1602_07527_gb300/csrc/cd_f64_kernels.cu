@@ -638,6 +638,59 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Explicit Jacobian (Eq. delements), for analysis: Theta(n^4) time and memory.
+//   dL_ij / dSigma_kl = S_ijk Linv_jl + (1 - delta_kl) S_ijl Linv_jk,
+//   S_ijk = sum_{m > j} L_im Linv_mk + L_ij Linv_jk / 2,   i >= j, k >= l,
+// with Sigma_kl and Sigma_lk one tied input.  Linv is lower triangular, so
+// the sum runs over max(j + 1, k) <= m <= i.
+// ---------------------------------------------------------------------------
+__global__ void k_jac_s(int n, const double *__restrict__ L, long long ldl, const double *__restrict__ Li,
+                        long long ldi, double *__restrict__ S) {
+  const long long total = (long long)n * n * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % n);
+    const long long r = e / n;
+    const int j = (int)(r % n), i = (int)(r / n);
+    double v = 0.0;
+    if (j <= i && k <= i) {
+      for (int m = max(j + 1, k); m <= i; ++m) v = fma(L[(long long)i * ldl + m], Li[(long long)m * ldi + k], v);
+      if (k <= j) v = fma(0.5 * L[(long long)i * ldl + j], Li[(long long)j * ldi + k], v);
+    }
+    S[e] = v;
+  }
+}
+
+__global__ void k_jac(int n, const double *__restrict__ Li, long long ldi, const double *__restrict__ S,
+                      double *__restrict__ J) {
+  const long long n2 = (long long)n * n, total = n2 * n2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(e % n), k = (int)((e / n) % n);
+    const long long ij = e / n2;
+    const int j = (int)(ij % n), i = (int)(ij / n);
+    double v = 0.0;
+    if (j <= i && l <= k) {
+      const double *Sij = S + ij * n;
+      v = Sij[k] * Li[(long long)j * ldi + l];
+      if (k != l) v = fma(Sij[l], Li[(long long)j * ldi + k], v);
+    }
+    J[e] = v;
+  }
+}
+
+cudaError_t launch_jacobian(int n, const double *L, long long ldl, const double *Li, long long ldi, double *S,
+                            double *J, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long n3 = (long long)n * n * n, n4 = n3 * n;
+  k_jac_s<<<(unsigned)std::min<long long>(8192, (n3 + 255) / 256), 256, 0, s>>>(n, L, ldl, Li, ldi, S);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_jac<<<(unsigned)std::min<long long>(65536, (n4 + 255) / 256), 256, 0, s>>>(n, Li, ldi, S, J);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
 __global__ void k_copy(const double *__restrict__ src, long long lds, double *__restrict__ dst, long long ldd,

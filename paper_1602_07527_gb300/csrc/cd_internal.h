@@ -130,5 +130,8 @@ cudaError_t launch_copy(const double *src, long long lds, double *dst, long long
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
 cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
+// Eq. delements: S (n^3 doubles) then J (n^4 doubles) from L and Linv = L^{-1}.
+cudaError_t launch_jacobian(int n, const double *L, long long ldl, const double *Li, long long ldi, double *S,
+                            double *J, cudaStream_t s);
 int gemm_ctas_per_sm(int ts);  // resident CTAs of the FP64 GEMM per SM (tile size ts)
 }  // namespace cd

@@ -76,6 +76,7 @@ def lib():
         L.cd_chol_fwd_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp]
         L.cd_chol_fwd_and_sens.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp, _vp]
         L.cd_chol_fwd_and_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp, _vp]
+        L.cd_chol_jacobian.argtypes = [_vp, _i, _vp, _ll, _vp, _vp]
         L.cd_get_last_device_error.argtypes = [_vp, P(_i)]
         L.cd_launch_count.argtypes = [_vp]
         L.cd_launch_count.restype = _ll
@@ -97,7 +98,7 @@ def exported_symbols():
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
             "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout",
-            "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched"]
+            "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched", "cd_chol_jacobian"]
 
 
 def handle(device=None):
@@ -242,6 +243,17 @@ def chol_fwd_and_sens(A, Adot, nb=0, prec="fp64", info=None, handle_=None, diag=
     _check(lib().cd_chol_fwd_and_sens(_h(handle_, dev), n, _vp(A.data_ptr()), lda, _vp(Adot.data_ptr()), ldd,
                                       ctypes.byref(o), _stream(dev), _vp(info.data_ptr())), "cd_chol_fwd_and_sens")
     return info
+
+
+def chol_jacobian(L, handle_=None):
+    """Eq. delements: the n x n x n x n tensor J[i, j, k, l] = dL_ij / dSigma_kl
+    (i >= j, k >= l; tied pairs Sigma_kl = Sigma_lk counted once), computed on
+    the device from the factor L.  Theta(n^4) memory: for analysis."""
+    n, ldl = _mat(L, "L")
+    J = torch.empty((n, n, n, n), dtype=torch.float64, device=L.device)
+    _check(lib().cd_chol_jacobian(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(J.data_ptr()),
+                                  _stream(L.device)), "cd_chol_jacobian")
+    return J
 
 
 def _arrays(mats, name):
