@@ -36,6 +36,15 @@
  *   torch.linalg.cholesky's backward is (tril + tril^T)/2 of the CD_OUT_TRIL
  *   result.
  *
+ * Triangle.  With options->uplo = CD_UPPER every "lower triangle" above reads
+ *   "upper triangle" and every factor is U = L^T (Sigma = U^T U): cd_chol_fwd
+ *   turns triu(Sigma) into U, cd_chol_rev turns U_bar = L_bar^T into
+ *   triu(Sigma_bar) = tril(Sigma_bar)^T, cd_chol_fwd_sens turns triu(Sigma_dot)
+ *   into U_dot; the strictly lower triangle is then neither read nor written
+ *   (except by CD_OUT_SYM).  The library transposes the operands into
+ *   workspace copies, runs the lower-triangle algorithms and transposes the
+ *   results back (two extra passes over each matrix).
+ *
  * Blocking.  options->nb (the paper's N_b, >= 1) is the block size; 0 picks
  *   a default.  The forward routines put a short block last and the reverse
  *   routine puts it first (top-left), as the paper does (Sec. 4.2).  Blocking
@@ -98,6 +107,12 @@ typedef enum {
                            diagonal block's inverse, spread over many CTAs     */
 } cd_diag;
 
+typedef enum {
+  CD_LOWER = 0, /* Sigma = L L^T, lower triangles referenced (the paper's form) */
+  CD_UPPER = 1  /* Sigma = U^T U with U = L^T, upper triangles referenced
+                   (LAPACK's uplo = 'U'); see "Triangle" above             */
+} cd_uplo;
+
 typedef struct {
   int nb;               /* block size N_b; 0 = library default                 */
   int prec;             /* a cd_precision value                                */
@@ -105,6 +120,7 @@ typedef struct {
   int diag;             /* a cd_diag value: the diagonal-block routine of the
                            reverse and forward-sensitivity passes (Sec. 4.2
                            allows either; both give the exact result)        */
+  int uplo;             /* a cd_uplo value                                     */
   long long spin_limit; /* bound on device-side wait iterations; 0 = default   */
 } cd_options;
 

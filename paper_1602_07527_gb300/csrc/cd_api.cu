@@ -1840,7 +1840,8 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   cd_options_default(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.nb < 0 || opt.prec < CD_FP64 || opt.prec > CD_MIXED_BF16X6 || opt.out < CD_OUT_TRIL ||
-      opt.out > CD_OUT_SYM || opt.diag < CD_DIAG_AUTO || opt.diag > CD_DIAG_SYMBOLIC)
+      opt.out > CD_OUT_SYM || opt.diag < CD_DIAG_AUTO || opt.diag > CD_DIAG_SYMBOLIC || opt.uplo < CD_LOWER ||
+      opt.uplo > CD_UPPER)
     return CD_EINVAL;
   int nmax = 0;
   for (int b = 0; b < batch; ++b) {
@@ -1868,6 +1869,10 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b)
       need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL);
+  const bool upper = opt.uplo == CD_UPPER;
+  const int narr = 1 + (factor ? 0 : 1) + (op == OP_DUAL ? 1 : 0);  // matrices per problem
+  if (upper)
+    for (int b = 0; b < batch; ++b) need += narr * (align_up(sizeof(double) * (size_t)n[b] * n[b]) + kAlign);
   int rc = ensure_ws(h, need, s);
   if (rc) return rc;
 
@@ -1881,6 +1886,23 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   c.side = h->side;
   c.part2 = (double *)ar.take(pb);
   c.part2_cap = pb / sizeof(double);
+  // CD_UPPER: each operand's upper triangle, transposed, in a workspace copy
+  // (ld n) on which the lower-triangle algorithms run; results go back below.
+  struct Copy {
+    double *user, *work;
+    long long ld;
+    int n;
+    bool out;
+  };
+  std::vector<Copy> copies;
+  auto staged = [&](const double *user, long long ld, int nn, bool out) -> double * {
+    double *w = (double *)ar.take(sizeof(double) * (size_t)nn * nn);
+    if (!w) return nullptr;
+    copies.push_back({const_cast<double *>(user), w, ld, nn, out});
+    c.launch("transpose_f64", 0.0, 16.0 * 0.5 * nn * (nn + 1.0),
+             [&] { return launch_transpose(user, ld, w, nn, nn, 0, s); });
+    return w;
+  };
   std::vector<Prob> P;
   P.reserve(batch);
   for (int b = 0; b < batch; ++b) {
@@ -1890,6 +1912,19 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     if (op == OP_DUAL) {
       p.Xd = Xd[b];
       p.ldxd = ldxd[b];
+    }
+    if (upper) {
+      p.X = staged(X[b], ldx[b], n[b], true);
+      p.ldx = n[b];
+      if (!factor) {
+        p.L = staged(L[b], ldl[b], n[b], false);
+        p.ldl = n[b];
+      }
+      if (op == OP_DUAL) {
+        p.Xd = staged(Xd[b], ldxd[b], n[b], true);
+        p.ldxd = n[b];
+      }
+      if (!p.X || (!factor && !p.L) || (op == OP_DUAL && !p.Xd)) return CD_ENOMEM;
     }
     P.push_back(p);
   }
@@ -1919,10 +1954,15 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
     c.s = s;
   }
   if (c.err) return c.err;
-  if (op == OP_REV && opt.out == CD_OUT_SYM)
+  const bool sym = op == OP_REV && opt.out == CD_OUT_SYM;
+  if (sym)
     for (auto &p : P)
       c.launch("mirror_f64", 0.0, 8.0 * p.n * (p.n - 1.0),
                [&] { return launch_mirror_lower(p.X, p.ldx, p.n, s); });
+  for (auto &cp : copies)  // CD_UPPER: results back to the upper triangles (every element for CD_OUT_SYM)
+    if (cp.out)
+      c.launch("transpose_f64", 0.0, 16.0 * 0.5 * cp.n * (cp.n + 1.0),
+               [&] { return launch_transpose(cp.work, cp.n, cp.user, cp.ld, cp.n, sym ? 2 : 1, s); });
   return c.err;
 }
 
@@ -1982,6 +2022,7 @@ void cd_options_default(cd_options *opt) {
   opt->prec = CD_FP64;
   opt->out = CD_OUT_TRIL;
   opt->diag = CD_DIAG_AUTO;
+  opt->uplo = CD_LOWER;
   opt->spin_limit = 0;
 }
 
@@ -2055,7 +2096,8 @@ int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size
   if (!h || !bytes || n_max < 0) return CD_EINVAL;
   const int nb = pick_nb(n_max, opt);
   *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64, true) +
-           ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0);
+           ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0) +
+           ((opt && opt->uplo == CD_UPPER) ? 3 * (align_up(sizeof(double) * (size_t)n_max * n_max) + kAlign) : 0);
   return CD_OK;
 }
 

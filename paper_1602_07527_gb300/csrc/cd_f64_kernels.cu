@@ -751,6 +751,36 @@ __global__ void k_mirror(double *A, long long lda, int n) {
   }
 }
 
+// dst(i, j) = src(j, i) through 32 x 32 shared tiles, both sides coalesced.
+// mode 0: the lower triangle of dst from the upper triangle of src (the
+// lower one of src is not read); mode 1: the upper triangle of dst from the
+// lower triangle of src; mode 2: every element.
+__global__ void k_transpose(const double *src, long long lds, double *dst, long long ldd, int n, int mode) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // destination tile: rows bi, columns bj
+  if ((mode == 0 && bj > bi) || (mode == 1 && bj < bi)) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int si = bj * 32 + r, sj = bi * 32 + tx;  // src(si, sj) = dst(sj, si)
+    const bool want = mode == 2 || (mode == 0 ? sj >= si : sj <= si);
+    tile[r][tx] = (si < n && sj < n && want) ? src[(long long)si * lds + sj] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    const bool want = mode == 2 || (mode == 0 ? j <= i : j >= i);
+    if (i < n && j < n && want) dst[(long long)i * ldd + j] = tile[tx][r];
+  }
+}
+
+cudaError_t launch_transpose(const double *src, long long lds, double *dst, long long ldd, int n, int mode,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nt = (n + 31) / 32;
+  k_transpose<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(src, lds, dst, ldd, n, mode);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
   const int nt = (n + 31) / 32;

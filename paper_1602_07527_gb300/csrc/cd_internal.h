@@ -128,6 +128,9 @@ cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s);
 cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, int rows,
                         int cols, cudaStream_t s);
 cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s);
+// dst(i, j) = src(j, i): mode 0 lower of dst from upper of src, 1 upper from lower, 2 all.
+cudaError_t launch_transpose(const double *src, long long lds, double *dst, long long ldd, int n, int mode,
+                             cudaStream_t s);
 cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
 // Eq. delements: S (n^3 doubles) then J (n^4 doubles) from L and Linv = L^{-1}.

@@ -37,7 +37,7 @@ class KernelStat(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int), ("diag", ctypes.c_int),
-                ("spin_limit", ctypes.c_longlong)]
+                ("uplo", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
 
 
 _lib = None
@@ -158,10 +158,14 @@ def _h(handle_, device):
     return handle_.ptr if isinstance(handle_, Handle) else handle_
 
 
-def options(nb=0, prec="fp64", out="tril", spin_limit=0, diag="auto"):
+UPLO = {"lower": 0, "upper": 1}
+
+
+def options(nb=0, prec="fp64", out="tril", spin_limit=0, diag="auto", uplo="lower"):
     o = Options()
     lib().cd_options_default(ctypes.byref(o))
     o.nb = int(nb)
+    o.uplo = UPLO[uplo] if isinstance(uplo, str) else int(uplo)
     o.diag = DIAG[diag] if isinstance(diag, str) else int(diag)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.out = OUT[out] if isinstance(out, str) else int(out)
@@ -188,7 +192,7 @@ def _check(rc, what):
         raise CholDiffError(rc, what)
 
 
-def chol_fwd(A, nb=0, prec="fp64", info=None, handle_=None):
+def chol_fwd(A, nb=0, prec="fp64", info=None, handle_=None, uplo="lower"):
     """In place: tril(A) = tril(Sigma) -> L (Sec. 4.2 chol_blocked).
 
     Returns the device int32 tensor holding LAPACK-style info (0 = success,
@@ -198,37 +202,37 @@ def chol_fwd(A, nb=0, prec="fp64", info=None, handle_=None):
     dev = A.device
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-    o = options(nb, prec)
+    o = options(nb, prec, uplo=uplo)
     _check(lib().cd_chol_fwd(_h(handle_, dev), n, _vp(A.data_ptr()), lda, ctypes.byref(o), _stream(dev),
                              _vp(info.data_ptr())), "cd_chol_fwd")
     return info
 
 
-def chol_rev(L, Abar, nb=0, prec="fp64", out="tril", handle_=None, diag="auto"):
+def chol_rev(L, Abar, nb=0, prec="fp64", out="tril", handle_=None, diag="auto", uplo="lower"):
     """In place: tril(Abar) = L_bar -> tril(Sigma_bar) (Sec. 4.2 chol_blocked_rev)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Abar, "Abar")
     if n != n2 or L.device != Abar.device:
         raise ValueError("L and Abar must have the same size and device")
-    o = options(nb, prec, out, diag=diag)
+    o = options(nb, prec, out, diag=diag, uplo=uplo)
     _check(lib().cd_chol_rev(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Abar.data_ptr()), lda,
                              ctypes.byref(o), _stream(L.device)), "cd_chol_rev")
     return Abar
 
 
-def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None, diag="auto"):
+def chol_fwd_sens(L, Adot, nb=0, prec="fp64", handle_=None, diag="auto", uplo="lower"):
     """In place: tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.2 chol_blocked_fwd)."""
     n, ldl = _mat(L, "L")
     n2, lda = _mat(Adot, "Adot")
     if n != n2 or L.device != Adot.device:
         raise ValueError("L and Adot must have the same size and device")
-    o = options(nb, prec, diag=diag)
+    o = options(nb, prec, diag=diag, uplo=uplo)
     _check(lib().cd_chol_fwd_sens(_h(handle_, L.device), n, _vp(L.data_ptr()), ldl, _vp(Adot.data_ptr()), lda,
                                   ctypes.byref(o), _stream(L.device)), "cd_chol_fwd_sens")
     return Adot
 
 
-def chol_fwd_and_sens(A, Adot, nb=0, prec="fp64", info=None, handle_=None, diag="auto"):
+def chol_fwd_and_sens(A, Adot, nb=0, prec="fp64", info=None, handle_=None, diag="auto", uplo="lower"):
     """In place, in one pass: tril(A) = tril(Sigma) -> L and
     tril(Adot) = tril(Sigma_dot) -> L_dot (Sec. 4.1-4.2: the forward-mode
     updates accumulated in the factorisation's loop).  Returns the info tensor."""
@@ -239,7 +243,7 @@ def chol_fwd_and_sens(A, Adot, nb=0, prec="fp64", info=None, handle_=None, diag=
     dev = A.device
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-    o = options(nb, prec, diag=diag)
+    o = options(nb, prec, diag=diag, uplo=uplo)
     _check(lib().cd_chol_fwd_and_sens(_h(handle_, dev), n, _vp(A.data_ptr()), lda, _vp(Adot.data_ptr()), ldd,
                                       ctypes.byref(o), _stream(dev), _vp(info.data_ptr())), "cd_chol_fwd_and_sens")
     return info
@@ -267,20 +271,20 @@ def _arrays(mats, name):
     return (b, (_i * b)(*ns), (_ll * b)(*lds), (_vp * b)(*ptrs), ns)
 
 
-def chol_fwd_batched(As, nb=0, prec="fp64", info=None, handle_=None):
+def chol_fwd_batched(As, nb=0, prec="fp64", info=None, handle_=None, uplo="lower"):
     b, n, ld, p, _ = _arrays(As, "A")
     if b == 0:
         return info
     dev = As[0].device
     if info is None:
         info = torch.zeros(b, dtype=torch.int32, device=dev)
-    o = options(nb, prec)
+    o = options(nb, prec, uplo=uplo)
     _check(lib().cd_chol_fwd_batched(_h(handle_, dev), b, n, p, ld, ctypes.byref(o), _stream(dev),
                                      _vp(info.data_ptr())), "cd_chol_fwd_batched")
     return info
 
 
-def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None, diag="auto"):
+def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None, diag="auto", uplo="lower"):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Abars, "Abar")
     if b != b2 or ns != ns2:
@@ -288,13 +292,13 @@ def chol_rev_batched(Ls, Abars, nb=0, prec="fp64", out="tril", handle_=None, dia
     if b == 0:
         return Abars
     dev = Ls[0].device
-    o = options(nb, prec, out, diag=diag)
+    o = options(nb, prec, out, diag=diag, uplo=uplo)
     _check(lib().cd_chol_rev_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_rev_batched")
     return Abars
 
 
-def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None, diag="auto"):
+def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None, diag="auto", uplo="lower"):
     b, n, ldl, pl, ns = _arrays(Ls, "L")
     b2, n2, lda, pa, ns2 = _arrays(Adots, "Adot")
     if b != b2 or ns != ns2:
@@ -302,13 +306,13 @@ def chol_fwd_sens_batched(Ls, Adots, nb=0, prec="fp64", handle_=None, diag="auto
     if b == 0:
         return Adots
     dev = Ls[0].device
-    o = options(nb, prec, diag=diag)
+    o = options(nb, prec, diag=diag, uplo=uplo)
     _check(lib().cd_chol_fwd_sens_batched(_h(handle_, dev), b, n, pl, ldl, pa, lda, ctypes.byref(o), _stream(dev)),
            "cd_chol_fwd_sens_batched")
     return Adots
 
 
-def chol_fwd_and_sens_batched(As, Adots, nb=0, prec="fp64", info=None, handle_=None, diag="auto"):
+def chol_fwd_and_sens_batched(As, Adots, nb=0, prec="fp64", info=None, handle_=None, diag="auto", uplo="lower"):
     b, n, lda, pa, ns = _arrays(As, "A")
     b2, n2, ldd, pd, ns2 = _arrays(Adots, "Adot")
     if b != b2 or ns != ns2:
@@ -318,7 +322,7 @@ def chol_fwd_and_sens_batched(As, Adots, nb=0, prec="fp64", info=None, handle_=N
     dev = As[0].device
     if info is None:
         info = torch.zeros(b, dtype=torch.int32, device=dev)
-    o = options(nb, prec, diag=diag)
+    o = options(nb, prec, diag=diag, uplo=uplo)
     _check(lib().cd_chol_fwd_and_sens_batched(_h(handle_, dev), b, n, pa, lda, pd, ldd, ctypes.byref(o),
                                               _stream(dev), _vp(info.data_ptr())), "cd_chol_fwd_and_sens_batched")
     return info
@@ -361,8 +365,8 @@ def device_error_of(handle_):
     return code.value
 
 
-def workspace_size(n, nb=0, prec="fp64", device=None):
-    o = options(nb, prec)
+def workspace_size(n, nb=0, prec="fp64", device=None, uplo="lower"):
+    o = options(nb, prec, uplo=uplo)
     out = ctypes.c_size_t()
     _check(lib().cd_workspace_size(handle(device), int(n), ctypes.byref(o), ctypes.byref(out)),
            "cd_workspace_size")
