@@ -369,6 +369,7 @@ struct TileBatch {
         case T_POTRF: flops += t * t * t / 3.0 * (g.d[p].inv ? 2.0 : 1.0); bytes += 2 * tri + (g.d[p].inv ? 8 * t * t : 0); break;
       }
     }
+    g.err = c.h->dev_err;
     c.launch(names[op], flops, bytes, [&] { return launch_tile_group(op, g, c.s); });
     g.count = 0;
   }

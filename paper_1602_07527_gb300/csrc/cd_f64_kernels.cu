@@ -370,11 +370,13 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
 // L as it is finished.  The tile is factorised right-looking in 16-column
 // panels (chol_blocked of Sec. 4.2 inside the tile):
 //   (a) the owners of the panel's diagonal-block rows send them to all CTAs;
-//   (b) every CTA factorises that block redundantly with four warps (one per
-//       sub-partition): per column one reciprocal square root by Goldschmidt's
-//       iteration (seven FP64 operations instead of a square root and a
-//       division), then the column scaled and the block's trailing entries
-//       updated one per thread -- all CTAs take the same pivot decisions;
+//   (b) every CTA factorises that block redundantly, pipelined over four
+//       warps (one per sub-partition): warp 0 forms each pivot's reciprocal
+//       square root by Goldschmidt's iteration (seven FP64 operations instead
+//       of a square root and a division), scales the column, publishes it and
+//       applies it to the next column at once (lookahead of one), while warps
+//       1-3 apply it to the later columns -- the pivot chain costs about nine
+//       FP64 operations per column, and all CTAs take the same pivot decisions;
 //   (c) each CTA solves its own rows of the panel, C <- C D^{-T}, by forward
 //       substitution across the 16 lanes of a half-warp (each step: one
 //       multiply by the pivot's reciprocal, a shuffle, one multiply-add), and
@@ -395,6 +397,42 @@ constexpr int kDgLd = kPb + 1;
 static_assert(kOwn == kPb && kOwn * kPb == kPotrfThreads && kNpMax <= kCl, "thread layout");
 constexpr size_t kPotrfSmem = sizeof(double) * (kLfN + kOwn * kTileMax + kPb * kDgLd + kTileMax +
                                                 kNpMax * kPb * kPb + kTileMax * kOwn + kPb * kOwn);
+
+// mbarrier helpers for the pipelined panel factorisation (shared memory, one CTA).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mb_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase of the given parity; gives up after 2 s, or at once
+// once *abort is set (a wait of the same CTA gave up), setting *abort.
+__device__ __forceinline__ void mb_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (mb_test(bar, parity)) return;
+  const unsigned long long t0 = now_ns();
+  while (!mb_test(bar, parity)) {
+    if (*abort) return;
+    if (now_ns() - t0 > 2000000000ULL) {
+      *abort = 1;
+      return;
+    }
+  }
+}
 
 // Exact binary32 -> binary64 of a normal positive float, with integer operations.
 __device__ __forceinline__ double pos_f32_to_f64(float f) {
@@ -458,6 +496,9 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double sm[];
   __shared__ int s_bad;
+  __shared__ volatile int s_tmo;
+  __shared__ __align__(8) uint64_t pub_bar, done_bar;
+  __shared__ double lcol[2 * kPb];
   const TileDesc &d = g.d[blockIdx.y];
   const int t = d.t;
   // Both exits below are taken by every CTA of the cluster alike (same
@@ -476,7 +517,14 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   double *Yt = Xc + kTileMax * kOwn;        // kPb x kOwn temporary
   const int nown = rank < t ? (t - 1 - rank) / kCl + 1 : 0;
   const int np = (t + kPb - 1) / kPb;
-  if (tid == 0) s_bad = -1;
+  if (tid == 0) {
+    s_bad = -1;
+    s_tmo = 0;
+    mb_init(&pub_bar, 1);
+    mb_init(&done_bar, 3);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   if (factor) {
     for (int e = tid; e < nown * kTileMax; e += blockDim.x) {
@@ -495,27 +543,53 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
         }
       }
       cluster.sync();
-      if (tid < 128) {  // (b) chol_unblocked of the block by warps 0-3, redundantly in every CTA
-        for (int c = 0; c < w; ++c) {
-          const double piv = Dg[c * kDgLd + c];
-          const long long pb = __double_as_longlong(piv);
-          const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;  // piv > 0 (false for NaN)
-          double rs = 0.0, sq = piv;
-          if (ok) rsqrt_sqrt(piv, rs, sq);
-          const int m = w - c - 1;
-          if (tid == 0) {
-            Lf[pk(c0 + c, c0 + c)] = ok ? sq : piv;
-            rd[c0 + c] = rs;
-            if (!ok && s_bad < 0) s_bad = c0 + c;
+      if (tid < 128) {  // (b) chol_unblocked of the block, redundantly in every CTA, pipelined:
+        // warp 0 (lanes = rows) forms each pivot's reciprocal square root,
+        // scales the column, publishes it, and applies it to the next column
+        // at once; warps 1-3 apply it to the columns after that.  g numbers
+        // the columns over all panels: the phases of the two mbarriers.
+        if (tid < 32) {
+          const int r = tid;
+          for (int c = 0; c < w; ++c) {
+            const int g = c0 + c;
+            const double piv = Dg[c * kDgLd + c];
+            const long long pb = __double_as_longlong(piv);
+            const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;  // piv > 0 (false for NaN)
+            double rs = 0.0, sq = piv;
+            if (ok) rsqrt_sqrt(piv, rs, sq);
+            const double l = (r > c && r < w) ? Dg[r * kDgLd + c] * rs : 0.0;
+            if (c >= 1) mb_wait(&done_bar, (uint32_t)(g - 1) & 1u, &s_tmo);  // workers' step g-1
+            if (r > c && r < w) {
+              Lf[pk(c0 + r, c0 + c)] = l;
+              lcol[(g & 1) * kPb + r] = l;
+            }
+            if (r == 0) {
+              Lf[pk(c0 + c, c0 + c)] = ok ? sq : piv;
+              rd[c0 + c] = rs;
+              if (!ok && s_bad < 0) s_bad = c0 + c;
+            }
+            __syncwarp();
+            if (r == 0) mb_arrive(&pub_bar);
+            const double lnext = __shfl_sync(0xffffffffu, l, c + 1 < 32 ? c + 1 : 0);
+            if (c + 1 < w && r >= c + 1 && r < w)  // column c+1 gets column c's update now
+              Dg[r * kDgLd + c + 1] = fma(-l, lnext, Dg[r * kDgLd + c + 1]);
+            __syncwarp();
           }
-          if (tid < m) Lf[pk(c0 + c + 1 + tid, c0 + c)] = Dg[(c + 1 + tid) * kDgLd + c] * rs;
-          if (tid < m * (m + 1) / 2) {  // trailing pair (r, k), c < k <= r < w
-            const int rr = tri_row(tid), kk = tid - rr * (rr + 1) / 2;
-            const int r = c + 1 + rr, k = c + 1 + kk;
-            const double arc = Dg[r * kDgLd + c] * (rs * rs);
-            Dg[r * kDgLd + k] = fma(-arc, Dg[k * kDgLd + c], Dg[r * kDgLd + k]);
+        } else {
+          const int e0 = tid - 32;
+          for (int c = 0; c < w; ++c) {
+            const int g = c0 + c;
+            mb_wait(&pub_bar, (uint32_t)g & 1u, &s_tmo);
+            const double *lc = lcol + (g & 1) * kPb;
+            const int m = w - c - 2;  // columns c+2 .. w-1
+            for (int e = e0; e < m * (m + 1) / 2; e += 96) {
+              const int rr = tri_row(e), kk = e - rr * (rr + 1) / 2;
+              const int r = c + 2 + rr, k = c + 2 + kk;
+              Dg[r * kDgLd + k] = fma(-lc[r], lc[k], Dg[r * kDgLd + k]);
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) mb_arrive(&done_bar);
           }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
         }
       }
       __syncthreads();
@@ -557,6 +631,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
       __syncthreads();
     }
     cluster.sync();
+    if (tid == 0 && s_tmo && g.err != nullptr) atomicExch(g.err, CD_ETIMEOUT);
     if (s_bad >= 0) {
       if (rank == 0 && tid == 0 && d.info != nullptr) *d.info = d.col0 + s_bad + 1;
       return;  // no remote store follows: each CTA may finish on its own

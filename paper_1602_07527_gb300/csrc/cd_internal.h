@@ -72,8 +72,10 @@ struct TileDesc {
 constexpr int kMaxTile = 48;
 struct TileGroup {
   int count, pad_;
+  int *err;  // device error word: CD_ETIMEOUT if a bounded wait of the cluster kernel runs out
   TileDesc d[kMaxTile];
 };
+static_assert(sizeof(TileGroup) <= 4096, "kernel parameter block too large");
 
 // T_REV / T_SENS: the level-2 derivative loops on one CTA.  T_POTRF: the
 // diagonal tile on a cluster of CTAs: factorise X in place (info set at the
