@@ -324,6 +324,22 @@ typedef struct {
 int cd_profile_enable(cd_handle *h, int on);
 int cd_profile_read(cd_handle *h, cd_kernel_stat *out, int max, int *count);
 
+/*
+ * The recorded launches one by one, in launch order, without clearing them
+ * (call it before cd_profile_read): out[0..*count) (at most `max`) gets each
+ * launch's kind, the stream it ran on (0 = the caller's stream, 1 = the
+ * handle's side stream) and its start and end in milliseconds from the
+ * first recorded launch's start.  Synchronises the handle's device.  Shows
+ * how the side stream's products overlap the diagonal chain.
+ */
+typedef struct {
+  char name[48];
+  int stream;
+  double start_ms, end_ms;
+} cd_launch_rec;
+
+int cd_profile_timeline(cd_handle *h, cd_launch_rec *out, int max, int *count);
+
 #ifdef __cplusplus
 }
 #endif

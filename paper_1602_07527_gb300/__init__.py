@@ -8,11 +8,11 @@ continuous-batching request loop.
 """
 from .native import (CholDiffError, chol_fwd, chol_fwd_and_sens, chol_fwd_and_sens_batched,  # noqa: F401
                      chol_fwd_batched, chol_fwd_sens, chol_fwd_sens_batched, chol_jacobian, chol_rev, chol_rev_batched, device_error,
-                     launch_count, profile_enable, profile_read, reserve, version,
+                     launch_count, profile_enable, profile_read, profile_timeline, reserve, version,
                      workspace_size)
 
 __all__ = ["CholDiffError", "chol_fwd", "chol_fwd_and_sens", "chol_fwd_and_sens_batched", "chol_fwd_batched",
            "chol_jacobian", "chol_fwd_sens", "chol_fwd_sens_batched",
-           "chol_rev", "chol_rev_batched", "device_error", "launch_count", "profile_enable", "profile_read",
+           "chol_rev", "chol_rev_batched", "device_error", "launch_count", "profile_enable", "profile_read", "profile_timeline",
            "reserve", "version",
            "workspace_size"]

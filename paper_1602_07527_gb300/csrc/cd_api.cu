@@ -106,6 +106,7 @@ struct Prob {
 struct Profiler {
   struct Rec {
     int kind;
+    int side;  // launched on the handle's side stream
     cudaEvent_t e0, e1;
     double flops, bytes;
   };
@@ -168,7 +169,7 @@ struct Ctx {
     const cudaError_t e = f();
     if (pr) {
       cudaEventRecord(e1, st);
-      pr->recs.push_back({pr->kind_id(kind), e0, e1, flops, bytes});
+      pr->recs.push_back({pr->kind_id(kind), (side && st == side) ? 1 : 0, e0, e1, flops, bytes});
     }
     check(e);
   }
@@ -1248,7 +1249,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     return k > 0;
   };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
-    {  // r1: W = C_bar D^{-1}; W -> C_bar; W and W^T split for r2, r3
+    {  // r1: C_bar <- C_bar D^{-1} (from the split copy of C_bar, so in place); then C_bar and C_bar^T split for r2, r3
       {
         SplitBatch sb(c);
         for (auto &p : P) {
@@ -1265,21 +1266,24 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+        double *Cb = p.X + (long long)k * p.ldx + j;
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
                0.0);
       }
     }
     {
-      CopyBatch cb(c);
       SplitBatch sb(c);
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
         if (m <= 0) continue;
-        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
-        sb.add(p.W, nb, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-        sb.add(p.W, nb, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, (int)p.mx.ldn, 0, 0, T);
+        const double *Cb = p.X + (long long)k * p.ldx + j;
+        sb.add(Cb, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        // C_bar^T is the K = m operand of r3 and r5a: its columns up to the next
+        // 64-wide K block are written (zeros past m), the rest is never read
+        const int kw = (int)std::min<long long>(p.mx.ldn, (m + 63) / 64 * 64);
+        sb.add(Cb, p.ldx, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, kw, 0, 0, T);
       }
     }
     c.fork();
@@ -1446,24 +1450,21 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
                0.0);
       }
     }
     {
-      CopyBatch cb(c);
       SplitBatch sb(c);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
         // the finished block column of L joins the split operand
         sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
               w, j, j, T);
       }
-      cb.flush();  // the solved panel must be in place before it is split
-      sb.flush();
     }
   }
 }
@@ -1578,23 +1579,20 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
                0.0);
       }
     }
     {
-      CopyBatch cb(c);
       SplitBatch sb(c);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
         sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
               w, j, j, T);
       }
-      cb.flush();  // the solved panel must be in place before it is split
-      sb.flush();
     }
   }
 }
@@ -1705,7 +1703,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     c.join();
-    {  // f4: W = C D^{-T}   (C -> P1, D^{-1} -> P4, tril(D_dot) -> P3 for g4)
+    {  // f4: C <- C D^{-T}   (C -> P1, D^{-1} -> P4, tril(D_dot) -> P3 for g4)
       {
         SplitBatch sb(c);
         for (auto &p : P) {
@@ -1723,23 +1721,20 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W, nb, 1.0,
+        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
                0.0);
       }
     }
-    {  // W -> C; the finished block column of L joins the split operand
-      CopyBatch cb(c);
+    {  // the finished block column of L joins the split operand
       SplitBatch sb(c);
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
-        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
         sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j, w, j,
                j, T);
       }
-      cb.flush();  // the solved panel must be in place before it is split
-      sb.flush();
     }
     {  // g4a: C_dot <- C_dot - C D_dot^T
       MixedBatch mb(c, T, false, false, "g4a");
@@ -1752,7 +1747,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                p.ldxd, -1.0, 1.0);
       }
     }
-    {  // g4b: W2 = C_dot D^{-T}
+    {  // g4b: C_dot <- C_dot D^{-T}
       {
         SplitBatch sb(c);
         for (auto &p : P) {
@@ -1768,23 +1763,20 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, p.W2, nb, 1.0,
+        double *Cb = p.Xd + (long long)k * p.ldxd + j;  // in place: the product reads only the split copies
+        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldxd, 1.0,
                0.0);
       }
     }
-    {  // W2 -> C_dot; the finished block column of L_dot joins its split operand
-      CopyBatch cb(c);
+    {  // the finished block column of L_dot joins its split operand
       SplitBatch sb(c);
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
-        cb.add(p.W2, nb, p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w);
         sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
                w, j, j, T);
       }
-      cb.flush();
-      sb.flush();
     }
   }
 }
@@ -2324,6 +2316,31 @@ int cd_profile_read(cd_handle *h, cd_kernel_stat *out, int max, int *count) {
     if (a.launches > 0 && k < max) out[k++] = a;
   *count = k;
   return rc;
+}
+
+int cd_profile_timeline(cd_handle *h, cd_launch_rec *out, int max, int *count) {
+  if (!h || !count || (max > 0 && !out)) return CD_EINVAL;
+  *count = 0;
+  Profiler *pr = (Profiler *)h->prof;
+  if (!pr || pr->recs.empty()) return CD_OK;
+  DeviceGuard guard(h->device);
+  if (cudaDeviceSynchronize() != cudaSuccess) return CD_ECUDA;
+  const cudaEvent_t t0 = pr->recs[0].e0;
+  int k = 0;
+  for (auto &r : pr->recs) {
+    if (k >= max) break;
+    cd_launch_rec &o = out[k++];
+    memset(&o, 0, sizeof(o));
+    snprintf(o.name, sizeof(o.name), "%s", pr->names[r.kind].c_str());
+    o.stream = r.side;
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, t0, r.e0) != cudaSuccess || cudaEventElapsedTime(&b, t0, r.e1) != cudaSuccess)
+      return CD_ECUDA;
+    o.start_ms = a;
+    o.end_ms = b;
+  }
+  *count = k;
+  return CD_OK;
 }
 
 }  // extern "C"

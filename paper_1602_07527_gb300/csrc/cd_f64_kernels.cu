@@ -43,16 +43,31 @@ __device__ __forceinline__ double load_b(const double *__restrict__ B, long long
   return (j >= k) ? B[(long long)j * ldb + k] : 0.0;
 }
 
-// One CTA computes a TS x TS output tile over its K range; each thread owns a
-// 4 x 4 micro-tile (rows ty + TS/4 r, columns tx + TS/4 c), so a warp reads
-// few A values (broadcast) and consecutive B values per k.  TS = 64 (256
-// threads) for ordinary products; TS = 32 (64 threads) for small ones, where
-// a 64 x 64 x 16 chunk alone would hold one SM's FP64 unit for ~16 us and too
-// few CTAs would share the product's work.
+// Threads of a CTA for output tile size TS: 256 for 64 x 64 tiles; 128 (four
+// warps, one per sub-partition's FP64 unit) for the 32 x 32 tiles of small
+// products.
+template <int TS>
+__host__ __device__ constexpr int gemm_threads() {
+  return TS == 64 ? 256 : 128;
+}
+
+// One CTA computes a TS x TS output tile over its K range; each thread owns an
+// RM x 4 micro-tile (rows ty + RT r, columns tx + CT c), so a warp reads few A
+// values (broadcast) and consecutive B values per k.  TS = 64 (256 threads,
+// 4 x 4) for ordinary products; TS = 32 (128 threads, 2 x 4) for small ones,
+// where a 64 x 64 x 16 chunk alone would hold one SM's FP64 unit for ~16 us
+// and too few CTAs would share the product's work.  Every FP64 instruction
+// holds its sub-partition's FP64 unit for ~64 cycles, so a CTA's latency is
+// set by the multiply-adds per warp: four warps halve it against two.
+//
+// gemm_tile is one such work item (output tile, K split): tile bid of the
+// group's tile list, computed by the whole CTA with the given shared-memory
+// staging, which is free again when it returns (every use of it ends with a
+// CTA barrier).
 template <int AM, int BM, bool LOWER, int TS>
-__global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant__ GemmGroup g) {
-  constexpr int TD = TS / 4, NT = TD * TD, LOADS = GBK * TS / NT;
-  const int bid = blockIdx.x;
+__device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*As)[TS + 1], double (*Bs)[TS + 1]) {
+  constexpr int NT = gemm_threads<TS>(), CT = TS / 4, RT = NT / CT, RM = TS / RT, LOADS = GBK * TS / NT;
+  static_assert(RT * RM == TS && LOADS * NT == GBK * TS, "tile layout");
   int p = 0;
   while (p + 1 < g.count && bid >= g.d[p + 1].tile_begin) ++p;
   const GemmDesc &d = g.d[p];
@@ -86,12 +101,10 @@ __global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant_
   const double *__restrict__ B = d.B;
   const long long lda = d.lda, ldb = d.ldb;
 
-  __shared__ double As[GBK][TS + 1];
-  __shared__ double Bs[GBK][TS + 1];
-  const int tid = threadIdx.x, tx = tid % TD, ty = tid / TD;
-  double acc[4][4];
+  const int tid = threadIdx.x, tx = tid % CT, ty = tid / CT;
+  double acc[RM][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
@@ -115,13 +128,13 @@ __global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant_
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
-      double a[4], b[4];
+      double a[RM], b[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + TD * r];
+      for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + RT * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + TD * c];
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + CT * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RM; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
@@ -130,12 +143,12 @@ __global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant_
 
   const double alpha = d.alpha, beta = d.beta;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = m0 + ty + TD * r;
+  for (int r = 0; r < RM; ++r) {
+    const int i = m0 + ty + RT * r;
     if (i >= M) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int j = n0 + tx + TD * c;
+      const int j = n0 + tx + CT * c;
       if (j >= N || (LOWER && j > i)) continue;
       if (d.splits == 1) {
         double v = alpha * acc[r][c];
@@ -149,36 +162,56 @@ __global__ void __launch_bounds__(TS *TS / 16) k_gemm_f64(const __grid_constant_
   }
 }
 
+template <int AM, int BM, bool LOWER, int TS>
+__global__ void __launch_bounds__(gemm_threads<TS>(), TS == 32 ? 6 : 1) k_gemm_f64(const __grid_constant__ GemmGroup g) {
+  __shared__ double As[GBK][TS + 1];
+  __shared__ double Bs[GBK][TS + 1];
+  gemm_tile<AM, BM, LOWER, TS>(g, blockIdx.x, As, Bs);
+}
+
 // Deterministic split-K reduction: Cout = beta Cin + sum_z part[z], z in order.
 template <bool LOWER>
-__global__ void k_reduce_f64(const __grid_constant__ GemmGroup g) {
-  const GemmDesc &d = g.d[blockIdx.y];
-  if (d.splits <= 1) return;
+__device__ __forceinline__ void reduce_desc(const GemmGroup &g, const GemmDesc &d, long long first, long long stride) {
   const long long total = (long long)d.M * d.N;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = first; e < total; e += stride) {
     const int i = (int)(e / d.N), j = (int)(e - (long long)i * d.N);
     if (LOWER && j > i) continue;
+    // Partials loaded eight at a time (independent loads in flight), summed
+    // in order.
     double s = 0.0;
-    for (int z = 0; z < d.splits; ++z) s += d.part[(long long)z * total + e];
+    for (int z0 = 0; z0 < d.splits; z0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = z0 + q < d.splits ? __ldcg(d.part + (long long)(z0 + q) * total + e) : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (z0 + q < d.splits) s += v[q];
+    }
     if (LOWER && g.phi && i == j) s *= 0.5;
     if (d.beta != 0.0) s = fma(d.beta, d.Cin[(long long)i * d.ldcin + j], s);
     d.Cout[(long long)i * d.ldcout + j] = s;
   }
 }
 
+template <bool LOWER>
+__global__ void k_reduce_f64(const __grid_constant__ GemmGroup g) {
+  const GemmDesc &d = g.d[blockIdx.y];
+  if (d.splits <= 1) return;
+  reduce_desc<LOWER>(g, d, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 template <int AM, int BM>
 static cudaError_t launch_gemm_ab(const GemmGroup &g, cudaStream_t s) {
   if (g.ts == 32) {
     if (g.lower)
-      k_gemm_f64<AM, BM, true, 32><<<g.total_tiles, 64, 0, s>>>(g);
+      k_gemm_f64<AM, BM, true, 32><<<g.total_tiles, gemm_threads<32>(), 0, s>>>(g);
     else
-      k_gemm_f64<AM, BM, false, 32><<<g.total_tiles, 64, 0, s>>>(g);
+      k_gemm_f64<AM, BM, false, 32><<<g.total_tiles, gemm_threads<32>(), 0, s>>>(g);
   } else {
     if (g.lower)
-      k_gemm_f64<AM, BM, true, 64><<<g.total_tiles, 256, 0, s>>>(g);
+      k_gemm_f64<AM, BM, true, 64><<<g.total_tiles, gemm_threads<64>(), 0, s>>>(g);
     else
-      k_gemm_f64<AM, BM, false, 64><<<g.total_tiles, 256, 0, s>>>(g);
+      k_gemm_f64<AM, BM, false, 64><<<g.total_tiles, gemm_threads<64>(), 0, s>>>(g);
   }
   return cudaGetLastError();
 }
@@ -202,12 +235,18 @@ cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s) {
 int gemm_ctas_per_sm(int ts) {
   int a = 0, b = 0;
   if (ts == 32) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 32>, 64, 0) != cudaSuccess) a = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 32>, 64, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 32>, gemm_threads<32>(), 0) !=
+        cudaSuccess)
+      a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 32>, gemm_threads<32>(), 0) !=
+        cudaSuccess)
       b = 1;
   } else {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 64>, 256, 0) != cudaSuccess) a = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 64>, 256, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemm_f64<A_N, B_N, false, 64>, gemm_threads<64>(), 0) !=
+        cudaSuccess)
+      a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gemm_f64<A_SYM2, B_N, false, 64>, gemm_threads<64>(), 0) !=
+        cudaSuccess)
       b = 1;
   }
   return std::max(1, std::min(a, b));

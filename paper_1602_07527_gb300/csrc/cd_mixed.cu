@@ -131,55 +131,66 @@ __device__ __forceinline__ double combine(double a, double cin, double alpha, do
   return fma(alpha, a, beta * cin);
 }
 
-// Writes rows [0, nrows) of one output column j (rows rbase + rr) from the
-// FP32 staging column stw[rr * ld], forming each value under mode COMB.
+// The epilogue stages each warp's accumulators 32 rows x kEpiCols columns at
+// a time (lane = row on the way in), so that the output can be written with
+// consecutive lanes on consecutive columns.  16 columns keep the staging at
+// 17 KB per CTA, which leaves room on the SM for an FP64 CTA of the diagonal
+// chain to run beside a tensor-core product.
+constexpr int kEpiCols = 16;
+constexpr int kEpiLd = kEpiCols + 1;
+
+// Writes the staged rows rr = r0 + 2 k (k < 16, rr < nrows) of one output
+// column j (rows rbase + rr) from the FP32 staging column stw[rr * ld],
+// forming each value under mode COMB.
 template <int COMB, bool LOWER>
-__device__ __forceinline__ void write_column(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j) {
+__device__ __forceinline__ void write_column(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j,
+                                             int r0) {
   constexpr bool kUseCin = COMB >= kAdd;
-  double cin[32];
-  const double *ci = d.Cin + (long long)rbase * d.ldcin + j;
+  double cin[16];
+  const double *ci = d.Cin + (long long)(rbase + r0) * d.ldcin + j;
 #pragma unroll
-  for (int rr = 0; rr < 32; ++rr) {
-    cin[rr] = (kUseCin && rr < nrows && !(LOWER && j > rbase + rr)) ? ci[0] : 0.0;
-    ci += d.ldcin;
+  for (int k = 0; k < 16; ++k) {
+    const int rr = r0 + 2 * k;
+    cin[k] = (kUseCin && rr < nrows && !(LOWER && j > rbase + rr)) ? ci[0] : 0.0;
+    ci += 2 * d.ldcin;
   }
-  double *co = d.Cout + (long long)rbase * d.ldcout + j;
+  double *co = d.Cout + (long long)(rbase + r0) * d.ldcout + j;
 #pragma unroll
-  for (int rr = 0; rr < 32; ++rr) {
-    if (rr < nrows && !(LOWER && j > rbase + rr))
-      *co = combine<COMB>(f32_to_f64(stw[rr * ld]), cin[rr], d.alpha, d.beta);
-    co += d.ldcout;
+  for (int k = 0; k < 16; ++k) {
+    const int rr = r0 + 2 * k;
+    if (rr < nrows && !(LOWER && j > rbase + rr)) *co = combine<COMB>(f32_to_f64(stw[rr * ld]), cin[k], d.alpha, d.beta);
+    co += 2 * d.ldcout;
   }
 }
 
-// The same for a 32 x 32 block in 16-byte accesses: lane l covers columns
-// j0 + 2 (l % 16) + {0, 1} of row pair member l / 16 (Cout, Cin 16-byte
+// The same for the staged 32 x 16 block in 16-byte accesses: lane l covers
+// columns j0 + 2 (l % 8) + {0, 1} of rows l / 8 + 4 k (Cout, Cin 16-byte
 // aligned, even leading dimensions, j0 even).  Non-LOWER tiles only.
 template <int COMB>
 __device__ __forceinline__ void write_block_v2(const MDesc &d, const float *stw, int ld, int rbase, int nrows, int j0,
                                                int ncols, int lane) {
   constexpr bool kUseCin = COMB >= kAdd;
-  const int c = 2 * (lane & 15), h = lane >> 4;
+  const int c = 2 * (lane & 7), h = lane >> 3;
   const bool col_ok = c < ncols;  // ncols even here
-  double2 cin[16];
+  double2 cin[8];
   const double *ci = d.Cin + (long long)(rbase + h) * d.ldcin + j0 + c;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < 8; ++k) {
     cin[k] = make_double2(0.0, 0.0);
-    if (kUseCin && col_ok && 2 * k + h < nrows) cin[k] = *reinterpret_cast<const double2 *>(ci);
-    ci += 2 * d.ldcin;
+    if (kUseCin && col_ok && 4 * k + h < nrows) cin[k] = *reinterpret_cast<const double2 *>(ci);
+    ci += 4 * d.ldcin;
   }
   double *co = d.Cout + (long long)(rbase + h) * d.ldcout + j0 + c;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int rr = 2 * k + h;
+  for (int k = 0; k < 8; ++k) {
+    const int rr = 4 * k + h;
     if (col_ok && rr < nrows) {
       double2 v;
       v.x = combine<COMB>(f32_to_f64(stw[rr * ld + c]), cin[k].x, d.alpha, d.beta);
       v.y = combine<COMB>(f32_to_f64(stw[rr * ld + c + 1]), cin[k].y, d.alpha, d.beta);
       *reinterpret_cast<double2 *>(co) = v;
     }
-    co += 2 * d.ldcout;
+    co += 4 * d.ldcout;
   }
 }
 
@@ -198,15 +209,15 @@ __device__ __forceinline__ void write_block_v2_any(int comb, const MDesc &d, con
 
 template <bool LOWER>
 __device__ __forceinline__ void write_column_any(int comb, const MDesc &d, const float *stw, int ld, int rbase,
-                                                 int nrows, int j) {
+                                                 int nrows, int j, int r0) {
   switch (comb) {
-    case kCopy: write_column<kCopy, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    case kNeg: write_column<kNeg, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    case kScale: write_column<kScale, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    case kAdd: write_column<kAdd, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    case kSub: write_column<kSub, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    case kAxpy: write_column<kAxpy, LOWER>(d, stw, ld, rbase, nrows, j); break;
-    default: write_column<kGeneral, LOWER>(d, stw, ld, rbase, nrows, j); break;
+    case kCopy: write_column<kCopy, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    case kNeg: write_column<kNeg, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    case kScale: write_column<kScale, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    case kAdd: write_column<kAdd, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    case kSub: write_column<kSub, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    case kAxpy: write_column<kAxpy, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
+    default: write_column<kGeneral, LOWER>(d, stw, ld, rbase, nrows, j, r0); break;
   }
 }
 
@@ -323,8 +334,7 @@ template <int T>
 __host__ __device__ constexpr uint32_t stage_bytes() {
   return 2u * T * kTileBytes;
 }
-// Epilogue staging: one 32 x 32 FP32 block per epilogue warp (padded rows).
-constexpr int kEpiLd = 33;
+// Epilogue staging: one 32 x kEpiCols FP32 block per epilogue warp (padded rows).
 constexpr size_t kEpiBytes = (size_t)kEpiWarps * 32 * kEpiLd * sizeof(float);
 template <int T>
 constexpr size_t dyn_smem() {
@@ -559,24 +569,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ M
         tmem_ld32(acc + (uint32_t)c0, r);
         tmem_ld32(acc + (uint32_t)(BN + c0), q);
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          stw[lane * kEpiLd + i] = x.nkb > 0 ? __uint_as_float(r[i]) + __uint_as_float(q[i]) : 0.0f;
-        __syncwarp();
-        // lane = output column; the warp writes its rows one at a time, coalesced
-        const int j0 = x.n0 + c0, j = j0 + lane;
-        const int ncols = min(32, d.N - j0);
-        if (d.splits > 1) {
-          if (j < d.N)
-            for (int rr = 0; rr < nrows; ++rr) {
-              const int i = rbase + rr;
-              if (!(LOWER && j > i)) d.part[((long long)x.z * d.M + i) * d.N + j] = stw[rr * kEpiLd + lane];
-            }
-        } else if (d.vec && !(LOWER && x.m0 == x.n0) && (ncols & 1) == 0) {
-          if (ncols > 0) write_block_v2_any(comb, d, stw, kEpiLd, rbase, nrows, j0, ncols, lane);
-        } else if (j < d.N) {
-          write_column_any<LOWER>(comb, d, stw + lane, kEpiLd, rbase, nrows, j);
+        for (int hh = 0; hh < 32 / kEpiCols; ++hh) {
+#pragma unroll
+          for (int i = 0; i < kEpiCols; ++i)
+            stw[lane * kEpiLd + i] =
+                x.nkb > 0 ? __uint_as_float(r[hh * kEpiCols + i]) + __uint_as_float(q[hh * kEpiCols + i]) : 0.0f;
+          __syncwarp();
+          // lane % 16 = output column, lane / 16 = row parity: coalesced row segments
+          const int j0 = x.n0 + c0 + hh * kEpiCols, col = lane & 15, r0 = lane >> 4, j = j0 + col;
+          const int ncols = min(kEpiCols, d.N - j0);
+          if (d.splits > 1) {
+            if (j < d.N)
+              for (int rr = r0; rr < nrows; rr += 2) {
+                const int i = rbase + rr;
+                if (!(LOWER && j > i)) d.part[((long long)x.z * d.M + i) * d.N + j] = stw[rr * kEpiLd + col];
+              }
+          } else if (d.vec && !(LOWER && x.m0 == x.n0) && (ncols & 1) == 0) {
+            if (ncols > 0) write_block_v2_any(comb, d, stw, kEpiLd, rbase, nrows, j0, ncols, lane);
+          } else if (j < d.N) {
+            write_column_any<LOWER>(comb, d, stw + col, kEpiLd, rbase, nrows, j, r0);
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -635,35 +649,49 @@ __global__ void k_mreduce(const __grid_constant__ MGroup g) {
 // and each further term the BF16 nearest to the remainder so far,
 // (hi - t0 - ...) + lo, formed in FP32: hi - t0 is exact, and adding lo
 // rounds at 2^-24 of the remainder, far below the last term kept.
-__device__ void split_body(const SplitArgs &a, long long first, long long stride) {
-  __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
-  const long long tstride = a.dst_rows * a.ldd;
-  const long long total = (long long)a.dst_h * a.dst_w;
+// The FP32 pieces hi + lo of destination element (rr, cc) of a split: the
+// source value it views, or zero outside the view (padding).
+__device__ __forceinline__ void split_load(const SplitArgs &a, int rr, int cc, float &hi, float &lo) {
   const int vr_n = a.transpose ? a.cols : a.rows;  // view extent in destination coordinates
   const int vc_n = a.transpose ? a.rows : a.cols;
-  for (long long e = first; e < total; e += stride) {
-    const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
-    const int vr = a.reg_r0 + rr - a.dst_r0, vc = a.reg_c0 + cc - a.dst_c0;
-    float hi = 0.0f, lo = 0.0f;
-    if (vr >= 0 && vc >= 0 && vr < vr_n && vc < vc_n) {
-      const int r = a.transpose ? vc : vr, c = a.transpose ? vr : vc;
-      const bool upper = r < c;
-      if (a.mode == 0 || !upper || a.mode == 2) {
-        const long long off = upper && a.mode == 2 ? (long long)c * a.lds + r : (long long)r * a.lds + c;
-        f64_to_f32x2(a.src[off], hi, lo);
-        if (a.mode == 2 && r == c) {  // doubled diagonal: exact in FP32
-          hi *= 2.0f;
-          lo *= 2.0f;
-        }
+  const int vr = a.reg_r0 + rr - a.dst_r0, vc = a.reg_c0 + cc - a.dst_c0;
+  hi = 0.0f;
+  lo = 0.0f;
+  if (vr >= 0 && vc >= 0 && vr < vr_n && vc < vc_n) {
+    const int r = a.transpose ? vc : vr, c = a.transpose ? vr : vc;
+    const bool upper = r < c;
+    if (a.mode == 0 || !upper || a.mode == 2) {
+      const long long off = upper && a.mode == 2 ? (long long)c * a.lds + r : (long long)r * a.lds + c;
+      f64_to_f32x2(a.src[off], hi, lo);
+      if (a.mode == 2 && r == c) {  // doubled diagonal: exact in FP32
+        hi *= 2.0f;
+        lo *= 2.0f;
       }
     }
-    const long long o = (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc;
-    const __nv_bfloat16 t0 = __float2bfloat16_rn(hi);
-    const float d0 = hi - __bfloat162float(t0);
-    const __nv_bfloat16 t1 = __float2bfloat16_rn(d0 + lo);
-    dst[o] = t0;
-    dst[tstride + o] = t1;
-    if (a.T == 3) dst[2 * tstride + o] = __float2bfloat16_rn((d0 - __bfloat162float(t1)) + lo);
+  }
+}
+
+// The T BF16 terms of one element from its FP32 pieces.
+__device__ __forceinline__ void split_store(const SplitArgs &a, int rr, int cc, float hi, float lo) {
+  __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
+  const long long tstride = a.dst_rows * a.ldd;
+  const long long o = (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc;
+  const __nv_bfloat16 t0 = __float2bfloat16_rn(hi);
+  const float d0 = hi - __bfloat162float(t0);
+  const __nv_bfloat16 t1 = __float2bfloat16_rn(d0 + lo);
+  dst[o] = t0;
+  dst[tstride + o] = t1;
+  if (a.T == 3) dst[2 * tstride + o] = __float2bfloat16_rn((d0 - __bfloat162float(t1)) + lo);
+}
+
+// One split, element by element (grid-stride loop over the destination region).
+__device__ void split_body(const SplitArgs &a, long long first, long long stride) {
+  const long long total = (long long)a.dst_h * a.dst_w;
+  for (long long e = first; e < total; e += stride) {
+    const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
+    float hi, lo;
+    split_load(a, rr, cc, hi, lo);
+    split_store(a, rr, cc, hi, lo);
   }
 }
 
@@ -685,8 +713,45 @@ struct SplitGroup {
 };
 static_assert(sizeof(SplitGroup) <= 4096, "kernel parameter block too large");
 
-__global__ void k_split_group(const __grid_constant__ SplitGroup g) {
-  split_body(g.a[blockIdx.y], (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+// Several splits, in 32 x 32 destination tiles (one split per blockIdx.y).
+// A transposed split reads its source tile row by row (coalesced: consecutive
+// threads take consecutive source columns) into shared memory and writes the
+// destination rows from there, so that both sides are contiguous.  The 8 KB
+// tile fits beside a tensor-core product's CTA on one SM.
+constexpr int kSplitTR = 32, kSplitTC = 32, kSplitThreads = 256;
+__global__ void __launch_bounds__(kSplitThreads) k_split_group(const __grid_constant__ SplitGroup g) {
+  const SplitArgs &a = g.a[blockIdx.y];
+  __shared__ float sh[2][kSplitTC][kSplitTR + 1];
+  const int tiles_c = (a.dst_w + kSplitTC - 1) / kSplitTC;
+  const int tiles = ((a.dst_h + kSplitTR - 1) / kSplitTR) * tiles_c;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int rr0 = (t / tiles_c) * kSplitTR, cc0 = (t % tiles_c) * kSplitTC;
+    const int h = min(kSplitTR, a.dst_h - rr0), w = min(kSplitTC, a.dst_w - cc0);
+    if (a.transpose) {
+      for (int e = threadIdx.x; e < kSplitTR * kSplitTC; e += kSplitThreads) {
+        const int cc = e / kSplitTR, rr = e - cc * kSplitTR;
+        float hi = 0.0f, lo = 0.0f;
+        if (rr < h && cc < w) split_load(a, rr0 + rr, cc0 + cc, hi, lo);
+        sh[0][cc][rr] = hi;
+        sh[1][cc][rr] = lo;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kSplitTR * kSplitTC; e += kSplitThreads) {
+        const int rr = e / kSplitTC, cc = e - rr * kSplitTC;
+        if (rr < h && cc < w) split_store(a, rr0 + rr, cc0 + cc, sh[0][cc][rr], sh[1][cc][rr]);
+      }
+      __syncthreads();
+    } else {
+      for (int e = threadIdx.x; e < kSplitTR * kSplitTC; e += kSplitThreads) {
+        const int rr = e / kSplitTC, cc = e - rr * kSplitTC;
+        if (rr < h && cc < w) {
+          float hi, lo;
+          split_load(a, rr0 + rr, cc0 + cc, hi, lo);
+          split_store(a, rr0 + rr, cc0 + cc, hi, lo);
+        }
+      }
+    }
+  }
 }
 
 bool encode_map(CUtensorMap *m, const MOp &op) {
@@ -850,11 +915,12 @@ cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t
       if ((long long)a[i].dst_h * a[i].dst_w <= 0) continue;
       if (a[i].T < 2 || a[i].T > 3 || !a[i].dst) return cudaErrorInvalidValue;
       g.a[g.count++] = a[i];
-      biggest = std::max(biggest, (long long)a[i].dst_h * a[i].dst_w);
+      biggest = std::max(biggest, (long long)((a[i].dst_h + kSplitTR - 1) / kSplitTR) *
+                                      ((a[i].dst_w + kSplitTC - 1) / kSplitTC));
     }
     if (g.count == 0) continue;
-    const long long blocks = std::min<long long>(4096, (biggest + 255) / 256);
-    k_split_group<<<dim3((unsigned)blocks, (unsigned)g.count), 256, 0, s>>>(g);
+    const long long blocks = std::max<long long>(1, std::min<long long>(4096, biggest));  // biggest: tiles
+    k_split_group<<<dim3((unsigned)blocks, (unsigned)g.count), kSplitThreads, 0, s>>>(g);
     if (launches) ++*launches;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

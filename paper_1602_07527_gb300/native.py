@@ -35,6 +35,11 @@ class KernelStat(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class LaunchRec(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("stream", ctypes.c_int), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("prec", ctypes.c_int), ("out", ctypes.c_int), ("diag", ctypes.c_int),
                 ("uplo", ctypes.c_int), ("spin_limit", ctypes.c_longlong)]
@@ -83,6 +88,7 @@ def lib():
         L.cd_version.restype = ctypes.c_char_p
         L.cd_profile_enable.argtypes = [_vp, _i]
         L.cd_profile_read.argtypes = [_vp, P(KernelStat), _i, P(_i)]
+        L.cd_profile_timeline.argtypes = [_vp, P(LaunchRec), _i, P(_i)]
         L.cd_chol_rev_noalloc.argtypes = [_i, _vp, _ll, _vp, _ll, _i, _i, _vp]
         L.cd_set_priorities.argtypes = [_vp, _i, _i]
         L.cd_debug_wait_timeout.argtypes = [_vp, _vp]
@@ -96,7 +102,7 @@ def exported_symbols():
     return ["cd_create", "cd_destroy", "cd_options_default", "cd_workspace_size", "cd_reserve",
             "cd_chol_fwd", "cd_chol_rev", "cd_chol_fwd_sens", "cd_chol_fwd_batched",
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
-            "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read",
+            "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read", "cd_profile_timeline",
             "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout",
             "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched", "cd_chol_jacobian"]
 
@@ -389,6 +395,16 @@ def profile_read(device=None, max_kinds=64):
     _check(lib().cd_profile_read(handle(device), arr, max_kinds, ctypes.byref(cnt)), "cd_profile_read")
     return [dict(name=arr[k].name.decode(), launches=int(arr[k].launches), ms=float(arr[k].ms),
                  flops=float(arr[k].flops), bytes=float(arr[k].bytes)) for k in range(cnt.value)]
+
+
+def profile_timeline(device=None, max_launches=200000):
+    """The recorded launches one by one (not cleared; call before profile_read):
+    list of dicts with name, stream (0 caller's, 1 side), start_ms, end_ms."""
+    arr = (LaunchRec * max_launches)()
+    cnt = _i()
+    _check(lib().cd_profile_timeline(handle(device), arr, max_launches, ctypes.byref(cnt)), "cd_profile_timeline")
+    return [dict(name=arr[k].name.decode(), stream=int(arr[k].stream), start_ms=float(arr[k].start_ms),
+                 end_ms=float(arr[k].end_ms)) for k in range(cnt.value)]
 
 
 def version():
