@@ -897,6 +897,30 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
+    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T).
+       // f1 and g1 are enqueued before the side stream's f3 and g3, so that their CTAs take SMs first.
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        const double *R = p.X + (long long)j * p.ldx, *Rd = p.Xd + (long long)j * p.ldxd;
+        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
+        gb.add(w, w, j, R, p.ldx, R, p.ldx, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        gb.add(w, w, j, Rd, p.ldxd, R, p.ldx, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
+      GemmBatch gb(c, A_N, B_T, true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *Dd = p.Xd + (long long)j * p.ldxd + j;
+        gb.add(w, w, j, p.X + (long long)j * p.ldx, p.ldx, p.Xd + (long long)j * p.ldxd, p.ldxd, Dd, p.ldxd, Dd,
+               p.ldxd, -1.0, 1.0);
+      }
+    }
     {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
       GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
       for (auto &p : P) {
@@ -917,29 +941,6 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int w = k - j, m = p.n - k;
         double *Cd = p.Xd + (long long)k * p.ldxd + j;
         gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.Xd + (long long)j * p.ldxd, p.ldxd, Cd, p.ldxd, Cd,
-               p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T)
-      GemmBatch gb(c, A_N, B_T, true);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        const double *R = p.X + (long long)j * p.ldx, *Rd = p.Xd + (long long)j * p.ldxd;
-        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
-        gb.add(w, w, j, R, p.ldx, R, p.ldx, D, p.ldx, D, p.ldx, -1.0, 1.0);
-        gb.add(w, w, j, Rd, p.ldxd, R, p.ldx, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
-      GemmBatch gb(c, A_N, B_T, true);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *Dd = p.Xd + (long long)j * p.ldxd + j;
-        gb.add(w, w, j, p.X + (long long)j * p.ldx, p.ldx, p.Xd + (long long)j * p.ldxd, p.ldxd, Dd, p.ldxd, Dd,
                p.ldxd, -1.0, 1.0);
       }
     }
@@ -1287,6 +1288,18 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     c.fork();
+    {  // r3: D_bar <- tril(D_bar) - tril(C_bar^T C).  Enqueued before the side stream's
+       // products so that its few CTAs take SMs first.
+      MixedBatch mb(c, T, true, false, "r3");
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *Db = p.X + (long long)j * p.ldx + j;
+        mb.add(mop(p.mx.P2, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, k + p.mx.pad, j), w, w, m, Db,
+               p.ldx, Db, p.ldx, -1.0, 1.0);
+      }
+    }
     {  // r5, first part (side stream): R_bar <- R_bar - C_bar^T B.  It needs
        // neither r3 nor r4, so it leaves the diagonal chain.
       MixedBatch mb(c, T, false, true, "r5a");
@@ -1309,17 +1322,6 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         double *Bb = p.X + (long long)k * p.ldx;
         mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), m, j, w, Bb, p.ldx,
                Bb, p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // r3: D_bar <- tril(D_bar) - tril(C_bar^T C)
-      MixedBatch mb(c, T, true, false, "r3");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *Db = p.X + (long long)j * p.ldx + j;
-        mb.add(mop(p.mx.P2, p.mx.ldn, nb, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, k + p.mx.pad, j), w, w, m, Db,
-               p.ldx, Db, p.ldx, -1.0, 1.0);
       }
     }
     {  // r4 as the products of Eq. symrevtril (problems that use them)
@@ -1388,6 +1390,17 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   const int steps = nblocks(nmax, nb);
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
+    {  // f1: D <- D - tril(R R^T), enqueued before the side stream's f3 so that its CTAs take SMs first
+      MixedBatch mb(c, T, true, false, "f1");
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, D, p.ldx, D,
+               p.ldx, -1.0, 1.0);
+      }
+    }
     {  // f3 (side stream): C <- C - B R^T
       MixedBatch mb(c, T, false, true, "f3");
       for (auto &p : P) {
@@ -1396,17 +1409,6 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
         double *C = p.X + (long long)k * p.ldx + j;
         mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), m, w, j, C, p.ldx, C,
-               p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // f1: D <- D - tril(R R^T)
-      MixedBatch mb(c, T, true, false, "f1");
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        double *D = p.X + (long long)j * p.ldx + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, D, p.ldx, D,
                p.ldx, -1.0, 1.0);
       }
     }
@@ -1484,6 +1486,19 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   const int steps = nblocks(nmax, nb);
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
+    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
+      // (enqueued before the side stream's g3, so that its CTAs take SMs first)
+      MixedBatch mb(c, T, true, false, "g1");
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        double *Dd = p.X + (long long)j * p.ldx + j;
+        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
+        mb.add(mop(a, p.mx.ldb, p.n, T, 0, j), mop(b, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldx, Dd, p.ldx, -1.0,
+               1.0);
+      }
+    }
     for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T
       MixedBatch mb(c, T, false, true, "g3");
       for (auto &p : P) {
@@ -1493,18 +1508,6 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         double *Cd = p.X + (long long)k * p.ldx + j;
         void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
         mb.add(mop(a, p.mx.ldb, p.n, T, 0, k), mop(b, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldx, Cd, p.ldx, -1.0,
-               1.0);
-      }
-    }
-    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
-      MixedBatch mb(c, T, true, false, "g1");
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        double *Dd = p.X + (long long)j * p.ldx + j;
-        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
-        mb.add(mop(a, p.mx.ldb, p.n, T, 0, j), mop(b, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldx, Dd, p.ldx, -1.0,
                1.0);
       }
     }
@@ -1612,6 +1615,30 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
+    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T).
+       // f1 and g1 are enqueued before the side stream's f3 and g3, so that their CTAs take SMs first.
+      MixedBatch mb(c, T, true, false, "f1+g1");
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
+        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
+        mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), R, w, w, j, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
+    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
+      MixedBatch mb(c, T, true, false, "g1");
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *Dd = p.Xd + (long long)j * p.ldxd + j;
+        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldxd,
+               Dd, p.ldxd, -1.0, 1.0);
+      }
+    }
     {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
       MixedBatch mb(c, T, false, true, "f3+g3");
       for (auto &p : P) {
@@ -1633,29 +1660,6 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         double *Cd = p.Xd + (long long)k * p.ldxd + j;
         mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldxd,
                Cd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T)
-      MixedBatch mb(c, T, true, false, "f1+g1");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
-        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
-        mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
-        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), R, w, w, j, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
-      MixedBatch mb(c, T, true, false, "g1");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *Dd = p.Xd + (long long)j * p.ldxd + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldxd,
-               Dd, p.ldxd, -1.0, 1.0);
       }
     }
     {  // f2: D <- chol_unblocked(D) and its inverse, FP64 (wide blocks: both diagonal steps by recursion)

@@ -728,17 +728,6 @@ cudaError_t launch_potrf_cluster_group(const TileGroup &g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t tile_kernels_init() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_tile<T_REV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem)))
-    return e;
-  return cudaSuccess;
-}
-
 cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s) {
   if (g.count <= 0) return cudaSuccess;
   switch (op) {
@@ -900,6 +889,38 @@ cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s)
   const int nt = (n + 31) / 32;
   k_mirror<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(A, lda, n);
   return cudaGetLastError();
+}
+
+// The small kernels of the diagonal chain (32 x 32 GEMM tiles, split-K
+// reductions, copies) ask for the largest shared-memory carveout: an SM
+// configured for a tensor-core product's 211 KB then still takes their CTAs
+// beside it.  With the default preference a kernel without shared memory
+// (a split-K reduction) was held until the SM's other work drained.
+template <class K>
+static cudaError_t carve(K *k) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+template <int AM, int BM>
+static cudaError_t carve_ab() {
+  cudaError_t e;
+  if ((e = carve(k_gemm_f64<AM, BM, true, 32>)) || (e = carve(k_gemm_f64<AM, BM, false, 32>))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t tile_kernels_init() {
+  cudaError_t e;
+  if ((e = carve_ab<A_N, B_N>()) || (e = carve_ab<A_N, B_T>()) || (e = carve_ab<A_N, B_TL>()) ||
+      (e = carve_ab<A_T, B_N>()) || (e = carve_ab<A_SYM2, B_N>()) || (e = carve_ab<A_TL, B_NL>()) ||
+      (e = carve_ab<A_SYM1, B_T>()) || (e = carve_ab<A_NL, B_NL>()) || (e = carve(k_reduce_f64<true>)) ||
+      (e = carve(k_reduce_f64<false>)) || (e = carve(k_copy)) || (e = carve(k_copy_group)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tile<T_REV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem)))
+    return e;
+  return cudaSuccess;
 }
 
 }  // namespace cd

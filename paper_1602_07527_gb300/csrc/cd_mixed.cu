@@ -398,13 +398,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 //                 tensor-memory accumulator sets (256 columns each: leading
 //                 product and corrections), alternating between units;
 //   warps 2-9     drain a finished accumulator set (each warp 32 tensor
-//                 memory lanes, i.e. rows, and half of the columns, 32 at a
-//                 time through shared memory) and write the FP64 output or
+//                 memory lanes, i.e. rows, and half of the columns, loaded
+//                 32 at a time and staged 16 at a time through shared
+//                 memory) and write the FP64 output or
 //                 FP32 split-K partials, while the MMA warp already fills the
 //                 other set.  Two warps per sub-partition hide each other's
 //                 load and store latency.
+//
+// At most 128 registers a thread (no spills): a sub-partition that holds
+// three of the ten warps then keeps 4K registers free, room for a warp of an
+// FP64 chain kernel or a reduction beside the product.
 template <int T, bool LOWER>
-__global__ void __launch_bounds__(kThreads, 1) k_mgemm(const __grid_constant__ MGroup g) {
+__global__ void __maxnreg__(128) k_mgemm(const __grid_constant__ MGroup g) {
   constexpr int S = stages<T>();
   constexpr uint32_t SB = stage_bytes<T>();
   extern __shared__ uint8_t smem_raw[];
@@ -808,6 +813,12 @@ int mixed_init() {
   if (!e) e = cudaFuncSetAttribute(k_mgemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<2>());
   if (!e) e = cudaFuncSetAttribute(k_mgemm<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<3>());
   if (!e) e = cudaFuncSetAttribute(k_mgemm<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem<3>());
+  // the reductions and splits run beside the products: same (largest) shared-memory carveout
+  const int carve = cudaSharedmemCarveoutMaxShared;
+  if (!e) e = cudaFuncSetAttribute(k_mreduce<true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  if (!e) e = cudaFuncSetAttribute(k_mreduce<false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  if (!e) e = cudaFuncSetAttribute(k_split_group, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  if (!e) e = cudaFuncSetAttribute(k_split, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CD_ECUDA;
