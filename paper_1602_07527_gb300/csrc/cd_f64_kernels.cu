@@ -21,7 +21,6 @@ namespace cd {
 // ---------------------------------------------------------------------------
 // Grouped GEMM
 // ---------------------------------------------------------------------------
-constexpr int GBK = 16;
 
 template <int AM>
 __device__ __forceinline__ double load_a(const double *__restrict__ A, long long lda, int i, int k) {
@@ -50,6 +49,12 @@ template <int TS>
 __host__ __device__ constexpr int gemm_threads() {
   return TS == 64 ? 256 : 128;
 }
+// K depth of a staged block: 16, or 8 for 32 x 32 tiles (4 KB of staging, so
+// that two such CTAs fit beside a tensor-core product's CTA on one SM).
+template <int TS>
+__host__ __device__ constexpr int gemm_kblock() {
+  return TS == 64 ? 16 : 8;
+}
 
 // One CTA computes a TS x TS output tile over its K range; each thread owns an
 // RM x 4 micro-tile (rows ty + RT r, columns tx + CT c), so a warp reads few A
@@ -66,8 +71,9 @@ __host__ __device__ constexpr int gemm_threads() {
 // CTA barrier).
 template <int AM, int BM, bool LOWER, int TS>
 __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*As)[TS + 1], double (*Bs)[TS + 1]) {
-  constexpr int NT = gemm_threads<TS>(), CT = TS / 4, RT = NT / CT, RM = TS / RT, LOADS = GBK * TS / NT;
-  static_assert(RT * RM == TS && LOADS * NT == GBK * TS, "tile layout");
+  constexpr int KB = gemm_kblock<TS>();
+  constexpr int NT = gemm_threads<TS>(), CT = TS / 4, RT = NT / CT, RM = TS / RT, LOADS = KB * TS / NT;
+  static_assert(RT * RM == TS && LOADS * NT == KB * TS, "tile layout");
   int p = 0;
   while (p + 1 < g.count && bid >= g.d[p + 1].tile_begin) ++p;
   const GemmDesc &d = g.d[p];
@@ -96,7 +102,7 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
   if (g.tri & TRI_B_LOWER) klo = max(klo, n0);
   if (g.tri & TRI_A_LOWER) khi = min(khi, m0 + TS);
   if (g.tri & TRI_B_UPPER) khi = min(khi, n0 + TS);
-  const int kfirst = kbeg + (klo - kbeg) / GBK * GBK;  // K blocks stay aligned to the split's start
+  const int kfirst = kbeg + (klo - kbeg) / KB * KB;  // K blocks stay aligned to the split's start
   const double *__restrict__ A = d.A;
   const double *__restrict__ B = d.B;
   const long long lda = d.lda, ldb = d.ldb;
@@ -108,12 +114,12 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
-  for (int k0 = kfirst; k0 < khi; k0 += GBK) {
+  for (int k0 = kfirst; k0 < khi; k0 += KB) {
 #pragma unroll
     for (int r = 0; r < LOADS; ++r) {
       const int e = tid + r * NT;
       int kk, ii;
-      if (AM == A_T) { ii = e % TS; kk = e / TS; } else { kk = e % GBK; ii = e / GBK; }
+      if (AM == A_T) { ii = e % TS; kk = e / TS; } else { kk = e % KB; ii = e / KB; }
       const int gi = m0 + ii, gk = k0 + kk;
       As[kk][ii] = (gi < M && gk < khi) ? load_a<AM>(A, lda, gi, gk) : 0.0;
     }
@@ -121,13 +127,13 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
     for (int r = 0; r < LOADS; ++r) {
       const int e = tid + r * NT;
       int kk, jj;
-      if (BM == B_N) { jj = e % TS; kk = e / TS; } else { kk = e % GBK; jj = e / GBK; }
+      if (BM == B_N) { jj = e % TS; kk = e / TS; } else { kk = e % KB; jj = e / KB; }
       const int gj = n0 + jj, gk = k0 + kk;
       Bs[kk][jj] = (gj < N && gk < khi) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
+    for (int kk = 0; kk < KB; ++kk) {
       double a[RM], b[4];
 #pragma unroll
       for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + RT * r];
@@ -163,9 +169,9 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
 }
 
 template <int AM, int BM, bool LOWER, int TS>
-__global__ void __launch_bounds__(gemm_threads<TS>(), TS == 32 ? 6 : 1) k_gemm_f64(const __grid_constant__ GemmGroup g) {
-  __shared__ double As[GBK][TS + 1];
-  __shared__ double Bs[GBK][TS + 1];
+__global__ void __launch_bounds__(gemm_threads<TS>(), TS == 32 ? 8 : 1) k_gemm_f64(const __grid_constant__ GemmGroup g) {
+  __shared__ double As[gemm_kblock<TS>()][TS + 1];
+  __shared__ double Bs[gemm_kblock<TS>()][TS + 1];
   gemm_tile<AM, BM, LOWER, TS>(g, blockIdx.x, As, Bs);
 }
 
