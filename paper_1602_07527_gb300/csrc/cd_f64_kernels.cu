@@ -520,6 +520,24 @@ __device__ __forceinline__ void rsqrt_sqrt(double x, double &rs, double &sq) {
   rs = scale_pow2(h, 1 - k);
 }
 
+// 1/x for a positive normal FP64 x in three FP64 operations: the FP32
+// reciprocal of x's significand m (truncated to 24 bits) starts one step of
+// the cubic iteration y <- y + y (e + e^2), e = 1 - m y (Householder's method
+// of order two), which takes the ~2^-23 start error e to ~e^3, below FP64
+// rounding; the exponent is applied with integer operations.  Subnormal,
+// infinite and very large x (whose reciprocal would be subnormal) divide.
+__device__ __forceinline__ double recip_pos(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52) & 0x7FF;
+  if (e == 0 || e >= 2045) return 1.0 / x;
+  const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));  // [1, 2)
+  const float mf = __uint_as_float((127u << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
+  const double y0 = pos_f32_to_f64(__frcp_rn(mf));  // in (0.5, 1]
+  const double em = fma(-m, y0, 1.0);
+  const double y = fma(y0, fma(em, em, em), y0);
+  return scale_pow2(y, 1023 - e);
+}
+
 // Inverse of the lower kPb x kPb block of Lf at (c0, c0) (w x w used, rest
 // zero) into Li (row major), given the reciprocals rd of its diagonal.  All
 // 256 threads: half-warp q (16 lanes = rows) sweeps column q forward.
@@ -543,7 +561,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   __shared__ int s_bad;
   __shared__ volatile int s_tmo;
   __shared__ __align__(8) uint64_t pub_bar, done_bar;
-  __shared__ double lcol[2 * kPb];
+  __shared__ double acol[2 * kPb], ucol[2 * kPb];
   const TileDesc &d = g.d[blockIdx.y];
   const int t = d.t;
   // Both exits below are taken by every CTA of the cluster alike (same
@@ -588,11 +606,15 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
         }
       }
       cluster.sync();
-      if (tid < 128) {  // (b) chol_unblocked of the block, redundantly in every CTA, pipelined:
-        // warp 0 (lanes = rows) forms each pivot's reciprocal square root,
-        // scales the column, publishes it, and applies it to the next column
-        // at once; warps 1-3 apply it to the columns after that.  g numbers
-        // the columns over all panels: the phases of the two mbarriers.
+      if (tid < 128) {  // (b) chol_unblocked of the block in its L D L^T form, redundantly in
+        // every CTA, pipelined: warp 0 (lanes = rows) forms pivot d's
+        // reciprocal (three FP64 operations), the column a scaled by it,
+        // u = a / d, publishes a and u, and applies them to the next column
+        // at once; warps 1-3 apply them to the columns after that,
+        // A(r, k) -= a(r) u(k).  The pivot chain is five FP64 operations a
+        // column; the unscaled columns stay in Dg and become L's columns
+        // a / sqrt(d) below, all at once.  g numbers the columns over all
+        // panels: the phases of the two mbarriers.
         if (tid < 32) {
           const int r = tid;
           for (int c = 0; c < w; ++c) {
@@ -600,24 +622,20 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
             const double piv = Dg[c * kDgLd + c];
             const long long pb = __double_as_longlong(piv);
             const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;  // piv > 0 (false for NaN)
-            double rs = 0.0, sq = piv;
-            if (ok) rsqrt_sqrt(piv, rs, sq);
-            const double l = (r > c && r < w) ? Dg[r * kDgLd + c] * rs : 0.0;
+            const double inv = ok ? recip_pos(piv) : 0.0;
+            const double a = (r > c && r < w) ? Dg[r * kDgLd + c] : 0.0;
+            const double u = a * inv;
             if (c >= 1) mb_wait(&done_bar, (uint32_t)(g - 1) & 1u, &s_tmo);  // workers' step g-1
             if (r > c && r < w) {
-              Lf[pk(c0 + r, c0 + c)] = l;
-              lcol[(g & 1) * kPb + r] = l;
+              acol[(g & 1) * kPb + r] = a;
+              ucol[(g & 1) * kPb + r] = u;
             }
-            if (r == 0) {
-              Lf[pk(c0 + c, c0 + c)] = ok ? sq : piv;
-              rd[c0 + c] = rs;
-              if (!ok && s_bad < 0) s_bad = c0 + c;
-            }
+            if (r == 0 && !ok && s_bad < 0) s_bad = c0 + c;
             __syncwarp();
             if (r == 0) mb_arrive(&pub_bar);
-            const double lnext = __shfl_sync(0xffffffffu, l, c + 1 < 32 ? c + 1 : 0);
+            const double unext = __shfl_sync(0xffffffffu, u, c + 1 < 32 ? c + 1 : 0);
             if (c + 1 < w && r >= c + 1 && r < w)  // column c+1 gets column c's update now
-              Dg[r * kDgLd + c + 1] = fma(-l, lnext, Dg[r * kDgLd + c + 1]);
+              Dg[r * kDgLd + c + 1] = fma(-a, unext, Dg[r * kDgLd + c + 1]);
             __syncwarp();
           }
         } else {
@@ -625,17 +643,32 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
           for (int c = 0; c < w; ++c) {
             const int g = c0 + c;
             mb_wait(&pub_bar, (uint32_t)g & 1u, &s_tmo);
-            const double *lc = lcol + (g & 1) * kPb;
+            const double *ac = acol + (g & 1) * kPb, *uc = ucol + (g & 1) * kPb;
             const int m = w - c - 2;  // columns c+2 .. w-1
             for (int e = e0; e < m * (m + 1) / 2; e += 96) {
               const int rr = tri_row(e), kk = e - rr * (rr + 1) / 2;
               const int r = c + 2 + rr, k = c + 2 + kk;
-              Dg[r * kDgLd + k] = fma(-lc[r], lc[k], Dg[r * kDgLd + k]);
+              Dg[r * kDgLd + k] = fma(-ac[r], uc[k], Dg[r * kDgLd + k]);
             }
             __syncwarp();
             if ((tid & 31) == 0) mb_arrive(&done_bar);
           }
         }
+      }
+      __syncthreads();
+      if (tid < w) {  // pivots: sqrt(d) on L's diagonal, 1/sqrt(d) for the scaling and (c)
+        const double piv = Dg[tid * kDgLd + tid];
+        const long long pb = __double_as_longlong(piv);
+        const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;
+        double rs = 0.0, sq = piv;
+        if (ok) rsqrt_sqrt(piv, rs, sq);
+        Lf[pk(c0 + tid, c0 + tid)] = ok ? sq : piv;
+        rd[c0 + tid] = rs;
+      }
+      __syncthreads();
+      for (int e = tid; e < w * w; e += blockDim.x) {  // L's columns below the diagonal: a / sqrt(d)
+        const int r = e / w, c = e - r * w;
+        if (r > c) Lf[pk(c0 + r, c0 + c)] = Dg[r * kDgLd + c] * rd[c0 + c];
       }
       __syncthreads();
       if (s_bad >= 0) break;  // the same in every CTA: all factorised the same block
