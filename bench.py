@@ -33,6 +33,9 @@ METRIC = "chol_rev TFLOP/s @N=8192 (FP64 vs mixed, err vs FP64); served fwd+rev 
 UNIT = "TFLOP/s"
 # FP64 is a plain-ALU (DFMA) path on GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# ncu, k_gemm_f64<N,T> (64 x 64 tiles) in the FP64 step at N=4096: 28.0 MB of DRAM traffic
+# (dram__bytes_read.sum + dram__bytes_write.sum) per launch of 0.734 GFLOP on average
+GEMM_NT_DRAM_BYTES_PER_FLOP = 28.0e6 / 0.734e9
 SE_SEED = 2
 
 
@@ -388,8 +391,15 @@ def run_ours(args):
     roofline = None
     if dom:
         achieved = dom["flops"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
+        # DRAM bytes per launch of the FP64 N,T product from ncu (dram__bytes_read.sum +
+        # dram__bytes_write.sum) at N=4096, scaled to this launch's average work
+        traffic = None
+        if dom["name"] == "gemm_f64<N,T>" and dom["launches"] > 0:
+            traffic = GEMM_NT_DRAM_BYTES_PER_FLOP * dom["flops"] / dom["launches"]
         roofline = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "traffic_source": ("ncu at N=4096 (two launches: 28.0 MB in 0.734 GFLOP), scaled by the "
+                                       "launch's flops" if traffic is not None else None),
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 pipe)",
                     "launches": dom["launches"], "ms_per_launch": dom["ms"] / max(1, dom["launches"]),
                     "share_of_timed_region": dom["ms"] / (t0.elapsed_time(t1))}
