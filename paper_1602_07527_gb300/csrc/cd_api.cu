@@ -382,7 +382,8 @@ struct CopyBatch {
   Ctx &c;
   CopyGroup g;
   double bytes = 0;
-  explicit CopyBatch(Ctx &ctx) : c(ctx) { memset(&g, 0, sizeof(g)); }
+  bool subsym;  // dst -= tril(src + src^T) instead of dst = src
+  explicit CopyBatch(Ctx &ctx, bool subsym_ = false) : c(ctx), subsym(subsym_) { memset(&g, 0, sizeof(g)); }
   void add(const double *src, long long lds, double *dst, long long ldd, int rows, int cols) {
     if (rows <= 0 || cols <= 0) return;
     if (g.count == kMaxCopy) flush();
@@ -392,7 +393,10 @@ struct CopyBatch {
   }
   void flush() {
     if (g.count == 0) return;
-    c.launch("copy_f64", 0.0, bytes, [&] { return launch_copy_group(g, c.s); });
+    if (subsym)
+      c.launch("subsym_f64", 0.0, bytes, [&] { return launch_subsym_group(g, c.s); });
+    else
+      c.launch("copy_f64", 0.0, bytes, [&] { return launch_copy_group(g, c.s); });
     g.count = 0;
     bytes = 0;
   }
@@ -1486,17 +1490,25 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   const int steps = nblocks(nmax, nb);
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
-    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
-      // (enqueued before the side stream's g3, so that its CTAs take SMs first)
-      MixedBatch mb(c, T, true, false, "g1");
+    {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T) = D_dot - tril(P + P^T), P = R_dot R^T:
+       // one product into T1, then the symmetric update (enqueued before the side stream's g3,
+       // so that its CTAs take SMs first)
+      {
+        MixedBatch mb(c, T, false, false, "g1");
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int w = std::min(p.n, j + nb) - j;
+          mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, nullptr, 0,
+                 p.T1, nb, 1.0, 0.0);
+        }
+      }
+      CopyBatch sym(c, true);
       for (auto &p : P) {
         const int j = s * nb;
-        if (j >= p.n) continue;
+        if (j >= p.n || j == 0) continue;  // j = 0: no columns to the left, no product
         const int w = std::min(p.n, j + nb) - j;
-        double *Dd = p.X + (long long)j * p.ldx + j;
-        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
-        mb.add(mop(a, p.mx.ldb, p.n, T, 0, j), mop(b, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldx, Dd, p.ldx, -1.0,
-               1.0);
+        sym.add(p.T1, nb, p.X + (long long)j * p.ldx + j, p.ldx, w, w);
       }
     }
     for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T

@@ -875,6 +875,31 @@ cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// dst(i, j) -= src(i, j) + src(j, i) on and below the diagonal of a square
+// block: D_dot <- D_dot - tril(P + P^T) with P = R_dot R^T, which is the
+// forward-sensitivity update g1 (R R_dot^T = P^T) from one product.
+__global__ void k_subsym_group(const __grid_constant__ CopyGroup g) {
+  const CopyDesc &d = g.d[blockIdx.y];
+  const long long total = (long long)d.rows * d.cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d.cols), j = (int)(e - (long long)i * d.cols);
+    if (j > i) continue;
+    double *o = d.dst + (long long)i * d.ldd + j;
+    *o -= d.src[(long long)i * d.lds + j] + d.src[(long long)j * d.lds + i];
+  }
+}
+
+cudaError_t launch_subsym_group(const CopyGroup &g, cudaStream_t s) {
+  if (g.count <= 0) return cudaSuccess;
+  long long biggest = 0;
+  for (int p = 0; p < g.count; ++p) biggest = std::max(biggest, (long long)g.d[p].rows * g.d[p].cols);
+  if (biggest <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>(1024, (biggest + 255) / 256);
+  k_subsym_group<<<dim3((unsigned)blocks, (unsigned)g.count), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
 // Strict upper triangle <- mirror of the strict lower one, through a 32 x 32
 // shared tile so that both the reads and the writes are coalesced.
 __global__ void k_mirror(double *A, long long lda, int n) {
@@ -951,7 +976,8 @@ cudaError_t tile_kernels_init() {
   if ((e = carve_ab<A_N, B_N>()) || (e = carve_ab<A_N, B_T>()) || (e = carve_ab<A_N, B_TL>()) ||
       (e = carve_ab<A_T, B_N>()) || (e = carve_ab<A_SYM2, B_N>()) || (e = carve_ab<A_TL, B_NL>()) ||
       (e = carve_ab<A_SYM1, B_T>()) || (e = carve_ab<A_NL, B_NL>()) || (e = carve(k_reduce_f64<true>)) ||
-      (e = carve(k_reduce_f64<false>)) || (e = carve(k_copy)) || (e = carve(k_copy_group)))
+      (e = carve(k_reduce_f64<false>)) || (e = carve(k_copy)) || (e = carve(k_copy_group)) ||
+      (e = carve(k_subsym_group)))
     return e;
   if ((e = cudaFuncSetAttribute(k_tile<T_REV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;

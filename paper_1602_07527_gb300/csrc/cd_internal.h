@@ -134,6 +134,8 @@ cudaError_t launch_mirror_lower(double *A, long long lda, int n, cudaStream_t s)
 cudaError_t launch_transpose(const double *src, long long lds, double *dst, long long ldd, int n, int mode,
                              cudaStream_t s);
 cudaError_t launch_copy_group(const CopyGroup &g, cudaStream_t s);
+// dst -= tril(src + src^T) for square blocks (rows == cols).
+cudaError_t launch_subsym_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
 // Eq. delements: S (n^3 doubles) then J (n^4 doubles) from L and Linv = L^{-1}.
 cudaError_t launch_jacobian(int n, const double *L, long long ldl, const double *Li, long long ldi, double *S,
