@@ -440,6 +440,7 @@ constexpr int kPotrfThreads = 256;
 constexpr int kLfN = kTileMax * (kTileMax + 1) / 2;
 constexpr int kDgLd = kPb + 1;
 static_assert(kOwn == kPb && kOwn * kPb == kPotrfThreads && kNpMax <= kCl, "thread layout");
+static_assert(kPotrfThreads == 256 && kOwn == 16, "the inverse's column pairs assume 8 warps x 2 columns");
 constexpr size_t kPotrfSmem = sizeof(double) * (kLfN + kOwn * kTileMax + kPb * kDgLd + kTileMax +
                                                 kNpMax * kPb * kPb + kTileMax * kOwn + kPb * kOwn);
 
@@ -737,7 +738,14 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
     }
   }
   cluster.sync();  // every CTA holds every block inverse; no remote store follows
-  const int rr = tid / kOwn, q = tid % kOwn, c = rank + kCl * q;
+  // Thread -> (row rr of a block row, own column q).  A warp takes two
+  // adjacent columns (one per half-warp), so its lanes share the K range of
+  // the substitution below instead of running to the longest of sixteen; the
+  // column pairs are dealt so that the two warps of a sub-partition (w and
+  // w + 4) hold one long and one short column pair between them.
+  const int warp = tid >> 5, lane = tid & 31;
+  const int q0 = warp < 4 ? 2 * warp : 22 - 2 * warp;
+  const int rr = lane & 15, q = q0 + (lane >> 4), c = rank + kCl * q;
   for (int bi = 0; bi < np; ++bi) {
     const int r0 = bi * kPb, wb = min(kPb, t - r0), r = r0 + rr;
     double y = 0.0;
@@ -749,8 +757,10 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
     __syncthreads();
     if (rr < wb) {
       double x = 0.0;
-      const double *Lb = Li + bi * kPb * kPb + rr * kPb;
-      for (int r2 = 0; r2 <= rr; ++r2) x = fma(Lb[r2], Yt[r2 * kOwn + q], x);
+      if (c <= r) {  // X(r, c) = 0 above the diagonal; never read there
+        const double *Lb = Li + bi * kPb * kPb + rr * kPb;
+        for (int r2 = 0; r2 <= rr; ++r2) x = fma(Lb[r2], Yt[r2 * kOwn + q], x);
+      }
       Xc[r * kOwn + q] = x;
     }
     __syncthreads();
