@@ -1064,7 +1064,7 @@ void split(Ctx &c, cudaStream_t st, const double *src, long long lds, int rows, 
   a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
   a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
   a.T = T;
-  c.launch("split_bf16", 0.0, (8.0 + 2.0 * T) * h * w, st, [&] { return mixed_split_launch(a, st); });
+  c.launch("split_bf16", 0.0, (8.0 + 2.0 * T) * h * w, st, [&] { return mixed_split_group_launch(&a, 1, st, nullptr); });
 }
 
 // Accumulates the operand splits of all problems of one phase into grouped launches.

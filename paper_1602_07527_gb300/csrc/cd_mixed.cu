@@ -654,8 +654,9 @@ __global__ void k_mreduce(const __grid_constant__ MGroup g) {
 // and each further term the BF16 nearest to the remainder so far,
 // (hi - t0 - ...) + lo, formed in FP32: hi - t0 is exact, and adding lo
 // rounds at 2^-24 of the remainder, far below the last term kept.
-// The FP32 pieces hi + lo of destination element (rr, cc) of a split: the
-// source value it views, or zero outside the view (padding).
+//
+// split_load: the FP32 pieces hi + lo of destination element (rr, cc) of a
+// split, the source value it views or zero outside the view (padding).
 __device__ __forceinline__ void split_load(const SplitArgs &a, int rr, int cc, float &hi, float &lo) {
   const int vr_n = a.transpose ? a.cols : a.rows;  // view extent in destination coordinates
   const int vc_n = a.transpose ? a.rows : a.cols;
@@ -689,27 +690,12 @@ __device__ __forceinline__ void split_store(const SplitArgs &a, int rr, int cc, 
   if (a.T == 3) dst[2 * tstride + o] = __float2bfloat16_rn((d0 - __bfloat162float(t1)) + lo);
 }
 
-// One split, element by element (grid-stride loop over the destination region).
-__device__ void split_body(const SplitArgs &a, long long first, long long stride) {
-  const long long total = (long long)a.dst_h * a.dst_w;
-  for (long long e = first; e < total; e += stride) {
-    const int rr = (int)(e / a.dst_w), cc = (int)(e - (long long)rr * a.dst_w);
-    float hi, lo;
-    split_load(a, rr, cc, hi, lo);
-    split_store(a, rr, cc, hi, lo);
-  }
-}
-
 // cuTensorMapEncodeTiled is a driver entry point; it is looked up through the
 // runtime (no link-time dependency on the driver library).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
-
-__global__ void k_split(const SplitArgs a) {
-  split_body(a, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
-}
 
 constexpr int kMaxSplit = 36;
 struct SplitGroup {
@@ -818,7 +804,6 @@ int mixed_init() {
   if (!e) e = cudaFuncSetAttribute(k_mreduce<true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (!e) e = cudaFuncSetAttribute(k_mreduce<false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (!e) e = cudaFuncSetAttribute(k_split_group, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-  if (!e) e = cudaFuncSetAttribute(k_split, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CD_ECUDA;
@@ -939,13 +924,5 @@ cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t
   return cudaSuccess;
 }
 
-cudaError_t mixed_split_launch(const SplitArgs &a, cudaStream_t s) {
-  const long long total = (long long)a.dst_h * a.dst_w;
-  if (total <= 0) return cudaSuccess;
-  if (a.T < 2 || a.T > 3 || !a.dst) return cudaErrorInvalidValue;
-  long long blocks = std::min<long long>(8192, (total + 255) / 256);
-  k_split<<<(unsigned)blocks, 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
 
 }  // namespace cd

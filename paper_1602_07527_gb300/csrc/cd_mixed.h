@@ -78,8 +78,7 @@ struct SplitArgs {
   int dst_r0, dst_c0;
   int T;
 };
-cudaError_t mixed_split_launch(const SplitArgs &a, cudaStream_t s);
-// Several independent splits in one launch.
+// Independent splits in one launch (count of them).
 cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t s, int *launches);
 
 }  // namespace cd
