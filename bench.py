@@ -88,12 +88,16 @@ def parse():
                          "(no timing, no JSON line); the factor it needs is computed first in FP64")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6"],
                     help="precision of the --profile-pass operation")
+    ap.add_argument("--timeline", action="store_true",
+                    help="with --profile-pass: warm up, then print the recorded pass's launch timeline")
     return ap.parse_args()
 
 
 def profile_pass(args):
     """One pass of one operation, for a profiler to capture: the FP64 SE workload
-    for --prec fp64, the Matern-5/2 workload for the split-BF16 precisions."""
+    for --prec fp64, the Matern-5/2 workload for the split-BF16 precisions.
+    With --timeline, a warm-up pass first, then the library's own launch
+    timeline of the recorded pass (kernel, stream, start and end) on stdout."""
     import torch
     import paper_1602_07527_gb300 as cd
     from paper_1602_07527_gb300 import workloads as W
@@ -106,26 +110,51 @@ def profile_pass(args):
     else:
         S, Lb = W.mixed_matern_case(n, 3)
         seed = 3
-    A = torch.tensor(np.tril(S), device=dev)
+    A0 = torch.tensor(np.tril(S), device=dev)
     del S
     op = args.profile_pass
     if op in ("fwd", "fwd_and_sens"):
-        if op == "fwd":
-            info = cd.chol_fwd(A, nb=args.nb, prec=args.prec)
-        else:
-            Ad = torch.tensor(np.tril(W.sigma_dot(n, seed)), device=dev)
-            info = cd.chol_fwd_and_sens(A, Ad, nb=args.nb, prec=args.prec, diag=args.diag)
+        Ad0 = torch.tensor(np.tril(W.sigma_dot(n, seed)), device=dev) if op == "fwd_and_sens" else None
+        L = None
     else:
-        info = cd.chol_fwd(A)  # the FP64 factor the derivative pass takes as input
+        L = A0.clone()
+        if int(cd.chol_fwd(L).item()) != 0:  # the FP64 factor the derivative pass takes as input
+            raise RuntimeError("factorisation reported a non-positive pivot")
+        X0 = torch.tensor(Lb if op == "rev" else np.tril(W.sigma_dot(n, seed)), device=dev)
+
+    def run():
+        if op == "fwd":
+            A = A0.clone()
+            return cd.chol_fwd(A, nb=args.nb, prec=args.prec)
+        if op == "fwd_and_sens":
+            A, Ad = A0.clone(), Ad0.clone()
+            return cd.chol_fwd_and_sens(A, Ad, nb=args.nb, prec=args.prec, diag=args.diag)
+        X = X0.clone()
         if op == "rev":
-            X = torch.tensor(Lb, device=dev)
-            cd.chol_rev(A, X, nb=args.nb, prec=args.prec, diag=args.diag)
+            cd.chol_rev(L, X, nb=args.nb, prec=args.prec, diag=args.diag)
         else:
-            X = torch.tensor(np.tril(W.sigma_dot(n, seed)), device=dev)
-            cd.chol_fwd_sens(A, X, nb=args.nb, prec=args.prec, diag=args.diag)
+            cd.chol_fwd_sens(L, X, nb=args.nb, prec=args.prec, diag=args.diag)
+        return None
+
+    if args.timeline:
+        run()
+        torch.cuda.synchronize()
+        cd.profile_read(dev)
+        cd.profile_enable(True, dev)
+    info = run()
     torch.cuda.synchronize()
-    if int(info.item()) != 0:
+    if info is not None and int(info.item()) != 0:
         raise RuntimeError("factorisation reported a non-positive pivot")
+    if args.timeline:
+        tl = cd.profile_timeline(dev)
+        cd.profile_read(dev)
+        cd.profile_enable(False, dev)
+        print(f"# launch timeline: {op} {args.prec} N={n} nb={args.nb or 'default'}: {len(tl)} launches, "
+              f"span {tl[-1]['end_ms'] if tl else 0.0:.3f} ms (per-launch CUDA events; stream 1 = side stream)")
+        print("stream  kernel                                   start_us    end_us   dur_us")
+        for r in tl:
+            print(f"{r['stream']:6d}  {r['name']:38s} {1e3 * r['start_ms']:9.1f} {1e3 * r['end_ms']:9.1f} "
+                  f"{1e3 * (r['end_ms'] - r['start_ms']):8.1f}")
     print(f"profile pass done: {op} {args.prec} N={n}", file=sys.stderr)
     return 0
 
