@@ -269,11 +269,51 @@ struct GemmBatch {
     }
     return best;
   }
+  // The work items of a 32 x 32-tile group with triangular operands whose K
+  // range is not empty (all items of problems without K splits, which write
+  // their output even when it is zero); false if there are too many to list.
+  static bool nonempty_items(const GemmGroup &sub, GemmItems &it) {
+    it.count = 0;
+    for (int p = 0; p < sub.count; ++p) {
+      const GemmDesc &d = sub.d[p];
+      const int per = sub.lower ? d.tiles_m * (d.tiles_m + 1) / 2 : d.tiles_m * d.tiles_n;
+      for (int z = 0; z < d.splits; ++z)
+        for (int rem = 0; rem < per; ++rem) {
+          int ti, tj;
+          if (sub.lower) {
+            ti = 0;
+            while ((ti + 1) * (ti + 2) / 2 <= rem) ++ti;
+            tj = rem - ti * (ti + 1) / 2;
+          } else {
+            ti = rem / d.tiles_n;
+            tj = rem % d.tiles_n;
+          }
+          const int m0 = ti * 32, n0 = tj * 32, kbeg = z * d.kchunk;
+          int klo = kbeg, khi = std::min(d.K, kbeg + d.kchunk);
+          if (sub.tri & TRI_A_UPPER) klo = std::max(klo, m0);
+          if (sub.tri & TRI_B_LOWER) klo = std::max(klo, n0);
+          if (sub.tri & TRI_A_LOWER) khi = std::min(khi, m0 + 32);
+          if (sub.tri & TRI_B_UPPER) khi = std::min(khi, n0 + 32);
+          if (d.splits > 1 && klo >= khi) continue;  // contributes nothing; its partial is not read
+          if (it.count == kMaxItems) return false;
+          it.bid[it.count++] = d.tile_begin + z * per + rem;
+        }
+    }
+    return true;
+  }
   void launch_sub(GemmGroup &sub, bool red, double flops, double bytes, double rbytes) {
     if (sub.count == 0) return;
     char name[48];
     snprintf(name, sizeof(name), "gemm_f64<%s,%s>%s%s%s", kAName[g.amode], kBName[g.bmode], g.lower ? "_tril" : "",
              g.phi ? "_phi" : "", sub.ts == 32 ? "_t32" : "");
+    if (sub.ts == 32 && sub.tri && red) {
+      static thread_local GemmItems it;
+      if (nonempty_items(sub, it) && it.count < sub.total_tiles) {
+        c.launch(name, flops, bytes, st, [&] { return launch_gemm_items(sub, it, st); });
+        c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
+        return;
+      }
+    }
     c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(sub, st); });
     if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
   }

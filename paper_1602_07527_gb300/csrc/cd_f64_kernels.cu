@@ -175,6 +175,15 @@ __global__ void __launch_bounds__(gemm_threads<TS>(), TS == 32 ? 8 : 1) k_gemm_f
   gemm_tile<AM, BM, LOWER, TS>(g, blockIdx.x, As, Bs);
 }
 
+// The same for the listed work items only (32 x 32 tiles).
+template <int AM, int BM, bool LOWER>
+__global__ void __launch_bounds__(gemm_threads<32>(), 8)
+    k_gemm_f64_items(const __grid_constant__ GemmGroup g, const __grid_constant__ GemmItems it) {
+  __shared__ double As[gemm_kblock<32>()][33];
+  __shared__ double Bs[gemm_kblock<32>()][33];
+  gemm_tile<AM, BM, LOWER, 32>(g, it.bid[blockIdx.x], As, Bs);
+}
+
 // Deterministic split-K reduction: Cout = beta Cin + sum_z part[z], z in order.
 template <bool LOWER>
 __device__ __forceinline__ void reduce_desc(const GemmGroup &g, const GemmDesc &d, long long first, long long stride) {
@@ -182,16 +191,29 @@ __device__ __forceinline__ void reduce_desc(const GemmGroup &g, const GemmDesc &
   for (long long e = first; e < total; e += stride) {
     const int i = (int)(e / d.N), j = (int)(e - (long long)i * d.N);
     if (LOWER && j > i) continue;
+    // The K splits that can contribute to this element's tile: with
+    // triangular operands the others hold zeros (or were not launched).
+    int zlo = 0, zhi = d.splits;
+    if (g.tri && g.ts > 0) {
+      const int m0 = i / g.ts * g.ts, n0 = j / g.ts * g.ts;
+      int klo = 0, khi = d.K;
+      if (g.tri & TRI_A_UPPER) klo = max(klo, m0);
+      if (g.tri & TRI_B_LOWER) klo = max(klo, n0);
+      if (g.tri & TRI_A_LOWER) khi = min(khi, m0 + g.ts);
+      if (g.tri & TRI_B_UPPER) khi = min(khi, n0 + g.ts);
+      zlo = klo / d.kchunk;
+      zhi = klo < khi ? min(d.splits, (khi + d.kchunk - 1) / d.kchunk) : zlo;
+    }
     // Partials loaded eight at a time (independent loads in flight), summed
     // in order.
     double s = 0.0;
-    for (int z0 = 0; z0 < d.splits; z0 += 8) {
+    for (int z0 = zlo; z0 < zhi; z0 += 8) {
       double v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = z0 + q < d.splits ? __ldcg(d.part + (long long)(z0 + q) * total + e) : 0.0;
+      for (int q = 0; q < 8; ++q) v[q] = z0 + q < zhi ? __ldcg(d.part + (long long)(z0 + q) * total + e) : 0.0;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (z0 + q < d.splits) s += v[q];
+        if (z0 + q < zhi) s += v[q];
     }
     if (LOWER && g.phi && i == j) s *= 0.5;
     if (d.beta != 0.0) s = fma(d.beta, d.Cin[(long long)i * d.ldcin + j], s);
@@ -220,6 +242,31 @@ static cudaError_t launch_gemm_ab(const GemmGroup &g, cudaStream_t s) {
       k_gemm_f64<AM, BM, false, 64><<<g.total_tiles, gemm_threads<64>(), 0, s>>>(g);
   }
   return cudaGetLastError();
+}
+
+template <int AM, int BM>
+static cudaError_t launch_items_ab(const GemmGroup &g, const GemmItems &it, cudaStream_t s) {
+  if (g.lower)
+    k_gemm_f64_items<AM, BM, true><<<it.count, gemm_threads<32>(), 0, s>>>(g, it);
+  else
+    k_gemm_f64_items<AM, BM, false><<<it.count, gemm_threads<32>(), 0, s>>>(g, it);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_items(const GemmGroup &g, const GemmItems &it, cudaStream_t s) {
+  if (g.count <= 0 || it.count <= 0) return cudaSuccess;
+  if (g.ts != 32 || it.count > kMaxItems) return cudaErrorInvalidValue;
+  switch (g.amode * 8 + g.bmode) {
+    case A_N * 8 + B_N: return launch_items_ab<A_N, B_N>(g, it, s);
+    case A_N * 8 + B_T: return launch_items_ab<A_N, B_T>(g, it, s);
+    case A_N * 8 + B_TL: return launch_items_ab<A_N, B_TL>(g, it, s);
+    case A_T * 8 + B_N: return launch_items_ab<A_T, B_N>(g, it, s);
+    case A_SYM2 * 8 + B_N: return launch_items_ab<A_SYM2, B_N>(g, it, s);
+    case A_TL * 8 + B_NL: return launch_items_ab<A_TL, B_NL>(g, it, s);
+    case A_SYM1 * 8 + B_T: return launch_items_ab<A_SYM1, B_T>(g, it, s);
+    case A_NL * 8 + B_NL: return launch_items_ab<A_NL, B_NL>(g, it, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s) {
@@ -977,7 +1024,9 @@ static cudaError_t carve(K *k) {
 template <int AM, int BM>
 static cudaError_t carve_ab() {
   cudaError_t e;
-  if ((e = carve(k_gemm_f64<AM, BM, true, 32>)) || (e = carve(k_gemm_f64<AM, BM, false, 32>))) return e;
+  if ((e = carve(k_gemm_f64<AM, BM, true, 32>)) || (e = carve(k_gemm_f64<AM, BM, false, 32>)) ||
+      (e = carve(k_gemm_f64_items<AM, BM, true>)) || (e = carve(k_gemm_f64_items<AM, BM, false>)))
+    return e;
   return cudaSuccess;
 }
 

@@ -55,6 +55,17 @@ struct GemmGroup {
 };
 static_assert(sizeof(GemmGroup) <= 4096, "kernel parameter block too large");
 
+// The work items of a 32 x 32-tile launch that contribute anything (tile
+// indices of the group's tile list): with triangular operands many K splits
+// of a tile are empty; launching only the others spreads the real work
+// evenly over the SMs (the empty splits' partial sums are skipped by the
+// reduction, which sums each tile's non-empty splits only).
+constexpr int kMaxItems = 2048;
+struct GemmItems {
+  int count, pad_;
+  int bid[kMaxItems];
+};
+
 // ---------------------------------------------------------------------------
 // One-CTA diagonal-tile kernels (t <= kTileMax, tile in shared memory).
 // ---------------------------------------------------------------------------
@@ -125,6 +136,8 @@ struct cd_handle {
 namespace cd {
 // Launchers (cd_f64_kernels.cu).  All return cudaError_t of the launch.
 cudaError_t launch_gemm_group(const GemmGroup &g, cudaStream_t s);
+// A 32 x 32-tile group restricted to the listed work items.
+cudaError_t launch_gemm_items(const GemmGroup &g, const GemmItems &it, cudaStream_t s);
 cudaError_t launch_reduce_group(const GemmGroup &g, cudaStream_t s);
 cudaError_t launch_tile_group(TileOp op, const TileGroup &g, cudaStream_t s);
 cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, int rows,
