@@ -2035,8 +2035,9 @@ int rev_in_scratch(int n, const double *L, long long ldl, double *Abar, long lon
   memset(&hh, 0, sizeof(hh));
   cudaGetDevice(&hh.device);
   hh.num_sms = num_sms;
-  hh.gemm_slots = 2 * num_sms;
-  hh.gemm_slots_small = gemm_ctas_per_sm(32) * num_sms;  // an occupancy query: no allocation
+  // the same partition as cd_create's handle (occupancy queries: no allocation)
+  hh.gemm_slots = gemm_ctas_per_sm(64) * num_sms;
+  hh.gemm_slots_small = gemm_ctas_per_sm(32) * num_sms;
   Arena ar;
   ar.base = (char *)scratch;
   ar.cap = scratch_bytes;

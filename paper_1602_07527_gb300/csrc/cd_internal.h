@@ -65,6 +65,9 @@ struct GemmItems {
   int count, pad_;
   int bid[kMaxItems];
 };
+// k_gemm_f64_items takes both blocks as __grid_constant__ parameters: above
+// the classic 4 KB limit, within the 32764 bytes CUDA 12.1+ allows.
+static_assert(sizeof(GemmGroup) + sizeof(GemmItems) <= 32764, "kernel parameter block too large");
 
 // ---------------------------------------------------------------------------
 // One-CTA diagonal-tile kernels (t <= kTileMax, tile in shared memory).

@@ -2,9 +2,9 @@
 // device memory.
 //
 // Some callers may not call cudaMalloc (or any allocating routine) at the
-// point where they need a gradient: code running while a CUDA graph is being
-// captured, a custom allocator's own callbacks, or an embedding that owns all
-// device memory and forbids the library from taking more.  For them this
+// point where they need a gradient: a custom allocator's own callbacks, or an
+// embedding that owns all device memory and forbids the library from taking
+// more.  For them this
 // entry point runs the same blocked reverse pass as cd_chol_rev, but all of
 // its scratch (the inverses of L's diagonal blocks, the solved panel and the
 // split-K partial sums) lives in one fixed device array declared below, so

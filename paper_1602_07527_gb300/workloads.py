@@ -112,7 +112,8 @@ def serving_stream(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
     """Poisson arrivals: list of (t_arrival_s, n, mixed: bool, request seed).
 
     n = round(exp(U[ln n_lo, ln n_hi])) (log-uniform); each request's own
-    matrices come from ``serving_request(n, request_seed)``.
+    matrices are drawn on the device from its request seed by the serving
+    loop.
     """
     g = rng(seed, 11)
     t, out, k = 0.0, [], 0
@@ -125,7 +126,3 @@ def serving_stream(seed: int = 5, rate: float = 2000.0, duration: float = 10.0,
         k += 1
     return out
 
-
-def serving_request(n: int, req_seed: int):
-    """One served request: SE covariance (ell 0.3 on [0,1]^3, jitter 1e-4) and L_bar."""
-    return se(n, req_seed, 3, 0.3, 1e-4), lbar(n, req_seed)

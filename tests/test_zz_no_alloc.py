@@ -47,16 +47,33 @@ def _case(n, seed):
 
 
 def test_noalloc_matches_allocating_entry_point_twice(native):
-    for n, nb, seed in ((1500, 0, 31), (700, 64, 32)):
+    # (n, nb, out): the largest allowed problem with its default block size
+    # (the scratch is fullest there), a smaller one at nb = 64, a column-by-
+    # column one at nb = 1 and the symmetric output form
+    for n, nb, out, seed in ((2048, 128, 0, 30), (1500, 0, 0, 31), (700, 64, 1, 32), (40, 1, 0, 33)):
         L, Lb = _case(n, seed)
         Ld = torch.tensor(L, device=DEV)
         ref = torch.tensor(Lb, device=DEV)
-        native.chol_rev(Ld, ref, nb=nb)            # allocating entry point
+        native.chol_rev(Ld, ref, nb=nb, out="sym" if out else "tril")  # allocating entry point
         got = torch.tensor(Lb, device=DEV)
-        assert _noalloc(native, Ld, got, nb=nb) == 0
+        assert _noalloc(native, Ld, got, nb=nb, out=out) == 0
         torch.cuda.synchronize()
-        err = oracle.rel_fro(got.cpu().numpy(), ref.cpu().numpy())
-        assert err <= TOL, (n, err)
+        g, r = got.cpu().numpy(), ref.cpu().numpy()
+        if out:
+            assert np.array_equal(g, g.T)
+            g, r = np.tril(g), np.tril(r)
+        err = oracle.rel_fro(g, r)
+        assert err <= TOL, (n, nb, out, err)
+
+
+def test_noalloc_matches_oracle_at_its_limit(native):
+    n = 2048
+    L, Lb = _case(n, 34)
+    got = torch.tensor(Lb, device=DEV)
+    assert _noalloc(native, torch.tensor(L, device=DEV), got, nb=128) == 0
+    torch.cuda.synchronize()
+    err = oracle.rel_fro(got.cpu().numpy(), oracle.chol_unblocked_rev(L, Lb))
+    assert err <= TOL, err
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(native):
