@@ -92,7 +92,13 @@ extern "C" {
 typedef enum {
   CD_FP64 = 0,          /* all FP64 (DFMA)                                    */
   CD_MIXED_BF16X3 = 1,  /* products as hi*hi + hi*lo + lo*hi, BF16 in, FP32 acc */
-  CD_MIXED_BF16X6 = 2   /* three-term split, 6 BF16 products, FP32 accumulate  */
+  CD_MIXED_BF16X6 = 2,  /* three-term split, 6 BF16 products, FP32 accumulate  */
+  CD_MIXED_FIXED4 = 3   /* factorisation products on fixed-point slices: four
+                           BF16 slices per element sharing one exponent per
+                           row, 13 products, leading sums exact in FP32 over
+                           windows of 512 of K and carried exactly in 64-bit
+                           integers (operands rounded to 2^-32 of their row maxima);
+                           derivative passes as CD_MIXED_BF16X6              */
 } cd_precision;
 
 typedef enum {
@@ -260,11 +266,12 @@ int cd_chol_rev_noalloc(int n, const double *L, long long ldl, double *Abar, lon
                         int nb, int out, void *stream);
 
 /*
- * Diagnostic: the split-BF16 tensor-core product used by the CD_MIXED_*
- * paths, exposed so that it can be tested alone (no counterpart in the
- * paper).  C (M x N, ldc) = A B^T with A (M x K, lda) and B (N x K, ldb), all
- * FP64 row-major device matrices; prec is CD_MIXED_BF16X3 or
- * CD_MIXED_BF16X6; lower != 0 (requires M == N) writes only i >= j.
+ * Diagnostic: the tensor-core products used by the CD_MIXED_* paths, exposed
+ * so that they can be tested alone (no counterpart in the paper).  C (M x N,
+ * ldc) = A B^T with A (M x K, lda) and B (N x K, ldb), all FP64 row-major
+ * device matrices; prec is CD_MIXED_BF16X3 or CD_MIXED_BF16X6 (split-BF16
+ * product) or CD_MIXED_FIXED4 (fixed-point slice product, each row's exponent
+ * taken from its maximum); lower != 0 (requires M == N) writes only i >= j.
  * Uses the handle's workspace; asynchronous on stream.
  */
 int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,

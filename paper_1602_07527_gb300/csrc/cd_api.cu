@@ -95,6 +95,10 @@ struct Prob {
     void *big, *big2, *P1, *P2, *P3, *P4;
     long long ldb, ldn;
     int pad, T;
+    // CD_MIXED_FIXED4 factorisation: fixed-point slices of L (fbig, rows of L),
+    // of the panel (fP1) and of D^{-1} (fP4), with their row exponents
+    void *fbig, *fP1, *fP4;
+    int *exL, *exP1, *exP4;
   } mx;
   double *T1, *T2;  // nb x nb temporaries of the symbolic diagonal step
   double *Xd;       // one-loop pass: tril(Sigma_dot) in, L_dot out (null otherwise)
@@ -1082,7 +1086,8 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // Phi / halving steps stay in FP64 (the kernels above).
 // ============================================================================
 constexpr int kMixMaxChunk = 2048;  // longest FP32 accumulation before an FP64 reduction
-constexpr int kMixMinKbPerSplit = 8;  // shortest K range (64-wide blocks) of one split-K part
+constexpr int kMixMinKbPerSplit = 8;
+constexpr int kFixedSlices = 4;  // CD_MIXED_FIXED4: fixed-point slices per operand  // shortest K range (64-wide blocks) of one split-K part
 
 MOp mop(void *base, long long ld, long long rows, int T, int x0, int y0) {
   MOp o;
@@ -1092,6 +1097,14 @@ MOp mop(void *base, long long ld, long long rows, int T, int x0, int y0) {
   o.T = T;
   o.x0 = x0;
   o.y0 = y0;
+  o.ex = nullptr;
+  return o;
+}
+
+// A view of a fixed-point slice array (4 slices) with its row exponents.
+MOp fop(void *base, long long ld, long long rows, const int *ex, int x0, int y0) {
+  MOp o = mop(base, ld, rows, 4, x0, y0);
+  o.ex = ex;
   return o;
 }
 
@@ -1104,6 +1117,7 @@ void split(Ctx &c, cudaStream_t st, const double *src, long long lds, int rows, 
   a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
   a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
   a.T = T;
+  a.ex = nullptr;
   c.launch("split_bf16", 0.0, (8.0 + 2.0 * T) * h * w, st, [&] { return mixed_split_group_launch(&a, 1, st, nullptr); });
 }
 
@@ -1121,6 +1135,7 @@ struct SplitBatch {
     a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
     a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
     a.T = T;
+    a.ex = nullptr;
     v.push_back(a);
     bytes += (8.0 + 2.0 * T) * h * w;
   }
@@ -1138,6 +1153,40 @@ struct SplitBatch {
   ~SplitBatch() { flush(); }
 };
 
+// Fixed-point splits (4 slices) of all problems of one phase: with
+// exponents computed from each destination row's region, or given.
+struct FSplitBatch {
+  Ctx &c;
+  bool compute;
+  std::vector<SplitArgs> v;
+  double bytes = 0;
+  FSplitBatch(Ctx &ctx, bool compute_exponents) : c(ctx), compute(compute_exponents) {}
+  void add(const double *src, long long lds, int rows, int cols, int mode, void *dst, long long ldd,
+           long long dst_rows, int reg_r0, int reg_c0, int h, int w, int dst_r0, int dst_c0, int *ex) {
+    if (h <= 0 || w <= 0) return;
+    SplitArgs a;
+    a.src = src; a.lds = lds; a.rows = rows; a.cols = cols; a.mode = mode; a.transpose = 0;
+    a.dst = dst; a.ldd = ldd; a.dst_rows = dst_rows;
+    a.reg_r0 = reg_r0; a.reg_c0 = reg_c0; a.dst_h = h; a.dst_w = w; a.dst_r0 = dst_r0; a.dst_c0 = dst_c0;
+    a.T = kFixedSlices;
+    a.ex = ex;
+    v.push_back(a);
+    bytes += (8.0 * (compute ? 2 : 1) + 8.0) * h * w;
+  }
+  void flush() {
+    if (v.empty()) return;
+    c.launch("split_fixed4", 0.0, bytes, [&] {
+      int l = 0;
+      const cudaError_t e = fixed_split_group_launch(v.data(), (int)v.size(), compute, c.s, &l);
+      if (l > 1) c.h->launches += l - 1;
+      return e;
+    });
+    v.clear();
+    bytes = 0;
+  }
+  ~FSplitBatch() { flush(); }
+};
+
 // Accumulates tensor-core products of one kind into grouped launches.
 struct MixedBatch {
   Ctx &c;
@@ -1150,8 +1199,9 @@ struct MixedBatch {
   MProblem v[kCap];
   int count = 0;
   const char *tag;  // the algorithm step, for the profile
-  MixedBatch(Ctx &ctx, int T_, bool lower_, bool on_side = false, const char *tag_ = nullptr)
-      : c(ctx), T(T_), lower(lower_), tag(tag_) {
+  bool fixed;       // fixed-point slice products (cd_fixed.cu); T is then 4
+  MixedBatch(Ctx &ctx, int T_, bool lower_, bool on_side = false, const char *tag_ = nullptr, bool fixed_ = false)
+      : c(ctx), T(T_), lower(lower_), tag(tag_), fixed(fixed_) {
     const bool side = on_side && c.side;
     st = side ? c.side : c.s;
     part = side ? c.part2 : c.part;
@@ -1172,8 +1222,12 @@ struct MixedBatch {
   }
   int choose_splits(const MProblem &P) const {
     const int slots = std::max(1, c.h->num_sms * mixed_ctas_per_sm());
-    const int tm = (P.M + 127) / 128, tn = (P.N + 127) / 128;
-    const long long t1 = lower ? tm * (tm + 1) / 2 : tm * tn;
+    const int tm = (P.M + 127) / 128, tn = fixed ? (P.N + 63) / 64 : (P.N + 127) / 128;
+    long long t1 = lower ? tm * (tm + 1) / 2 : tm * tn;
+    if (fixed && lower) {
+      t1 = 0;
+      for (int ti = 0; ti < tm; ++ti) t1 += std::min(tn, 2 * ti + 2);
+    }
     const int kblocks = (P.K + 63) / 64;
     int sg = 1;
     if (t1 < 4LL * slots) {
@@ -1186,18 +1240,21 @@ struct MixedBatch {
         if (e > best + 0.02) { sg = s2; best = e; }
       }
     }
+    if (fixed) return std::min(sg, kblocks);  // exact over any K: splits only for parallelism
     return std::max((P.K + kMixMaxChunk - 1) / kMixMaxChunk, std::min(sg, kblocks));
   }
   void launch_range(int b, int e, double flops, double bytes) {
     if (e <= b) return;
-    const int prods = T == 3 ? 6 : 3;
+    const int prods = fixed ? 13 : T == 3 ? 6 : 3;
     char name[48];
-    snprintf(name, sizeof(name), "mgemm_bf16x%d%s%s%s", prods, lower ? "_tril" : "", tag ? " " : "", tag ? tag : "");
+    snprintf(name, sizeof(name), "%s%d%s%s%s", fixed ? "fgemm_fixed4x" : "mgemm_bf16x", prods, lower ? "_tril" : "",
+             tag ? " " : "", tag ? tag : "");
     c.launch(name, flops, bytes, st, [&] {
       int l = 0;
       const bool bulk = c.side && st == c.side;
-      cudaError_t err = mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l, 0,
-                                          bulk ? kUnitsPerCtaBulk : kUnitsPerCtaChain);
+      const int mu = bulk ? kUnitsPerCtaBulk : kUnitsPerCtaChain;
+      cudaError_t err = fixed ? fixed_gemm_launch(v + b, e - b, lower, c.h->dev_err, st, &l, 2 * mu)
+                              : mixed_gemm_launch(v + b, e - b, T, lower, c.h->dev_err, st, &l, 0, mu);
       if (l > 1) c.h->launches += l - 1;
       return err;
     });
@@ -1206,7 +1263,7 @@ struct MixedBatch {
     if (count == 0) return;
     size_t used = 0;
     double flops = 0, bytes = 0;
-    const int prods = T == 3 ? 6 : 3;
+    const int prods = fixed ? 13 : T == 3 ? 6 : 3;
     int begin = 0;
     for (int i = 0; i < count; ++i) {
       MProblem &P = v[i];
@@ -1243,16 +1300,24 @@ struct MixedBatch {
   ~MixedBatch() { flush(); }
 };
 
-int mix_terms(int prec) { return prec == CD_MIXED_BF16X6 ? 3 : 2; }
+// Split-BF16 terms of the products (CD_MIXED_FIXED4 keeps the three-term
+// split for the derivative passes and fixed-point slices for the factor).
+int mix_terms(int prec) { return prec == CD_MIXED_BF16X3 ? 2 : 3; }
+size_t fixed_bytes(int n, int nb) {
+  if (n <= 0) return 0;
+  const size_t ldb = (size_t)((n + 63) / 64 * 64);
+  const size_t e = (size_t)n * ldb + (size_t)n * nb + (size_t)nb * nb;
+  return 2 * (size_t)kFixedSlices * e + sizeof(int) * (2 * (size_t)n + nb) + 8 * kAlign;
+}
 
-size_t mix_bytes(int n, int nb, int T, bool two_big) {
+size_t mix_bytes(int n, int nb, int T, bool two_big, bool fixed = false) {
   if (n <= 0) return 0;
   const size_t ldb = (size_t)((n + 8 + 63) / 64 * 64), ldn = (size_t)((n + 63) / 64 * 64 + 64);
   const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + (size_t)nb * nb;
-  return 2 * (size_t)T * e + 8 * kAlign;
+  return 2 * (size_t)T * e + 8 * kAlign + (fixed ? fixed_bytes(n, nb) : 0);
 }
 
-bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar) {
+bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bool fixed = false) {
   for (auto &p : P) {
     memset(&p.mx, 0, sizeof(p.mx));
     if (p.n <= 0) continue;
@@ -1269,6 +1334,16 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar) {
     p.mx.P3 = ar.take(t * nb * p.mx.ldn);
     p.mx.P4 = ar.take(t * nb * nb);
     if (!p.mx.big || (two_big && !p.mx.big2) || !p.mx.P1 || !p.mx.P2 || !p.mx.P3 || !p.mx.P4) return false;
+    if (fixed) {
+      const size_t f = 2 * (size_t)kFixedSlices, ldf = (size_t)((n + 63) / 64 * 64);
+      p.mx.fbig = ar.take(f * n * ldf);
+      p.mx.fP1 = ar.take(f * n * nb);
+      p.mx.fP4 = ar.take(f * nb * nb);
+      p.mx.exL = (int *)ar.take(sizeof(int) * n);
+      p.mx.exP1 = (int *)ar.take(sizeof(int) * n);
+      p.mx.exP4 = (int *)ar.take(sizeof(int) * nb);
+      if (!p.mx.fbig || !p.mx.fP1 || !p.mx.fP4 || !p.mx.exL || !p.mx.exP1 || !p.mx.exP4) return false;
+    }
   }
   return true;
 }
@@ -1429,31 +1504,37 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // are split into `big` block column by block column.
 void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   const int T = P.empty() ? 2 : P[0].mx.T;
+  const bool fx = c.opt->prec == CD_MIXED_FIXED4;
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
+  if (fx)  // row exponents of L from the diagonal of Sigma, before it is overwritten
+    for (auto &p : P)
+      c.launch("diag_exponents", 0.0, 12.0 * p.n,
+               [&] { return fixed_diag_exponents(p.X, p.ldx, p.n, p.mx.exL, c.s); });
+  auto Lop = [&](const Prob &p, int x0, int y0) {
+    return fx ? fop(p.mx.fbig, (p.n + 63) / 64 * 64, p.n, p.mx.exL, x0, y0) : mop(p.mx.big, p.mx.ldb, p.n, T, x0, y0);
+  };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
     {  // f1: D <- D - tril(R R^T), enqueued before the side stream's f3 so that its CTAs take SMs first
-      MixedBatch mb(c, T, true, false, "f1");
+      MixedBatch mb(c, T, true, false, "f1", fx);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, D, p.ldx, D,
-               p.ldx, -1.0, 1.0);
+        mb.add(Lop(p, 0, j), Lop(p, 0, j), w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
       }
     }
     {  // f3 (side stream): C <- C - B R^T
-      MixedBatch mb(c, T, false, true, "f3");
+      MixedBatch mb(c, T, false, true, "f3", fx);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
         double *C = p.X + (long long)k * p.ldx + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), m, w, j, C, p.ldx, C,
-               p.ldx, -1.0, 1.0);
+        mb.add(Lop(p, 0, k), Lop(p, 0, j), m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
       }
     }
     {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
@@ -1480,7 +1561,17 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     c.join();
     {  // f4: C <- C tril(D)^{-T}
-      {
+      if (fx) {
+        FSplitBatch sb(c, true);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, p.mx.fP1, nb, p.n, 0, 0, m, nb, 0, 0, p.mx.exP1);
+          sb.add(p.dinv, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
+        }
+      } else {
         SplitBatch sb(c);
         for (auto &p : P) {
           const int j = s * nb;
@@ -1491,25 +1582,39 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false, false, "f4");
+      MixedBatch mb(c, T, false, false, "f4", fx);
       for (auto &p : P) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
         double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
-               0.0);
+        if (fx)
+          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, 0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), m, w, w, nullptr, 0,
+                 Cb, p.ldx, 1.0, 0.0);
+        else
+          mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
+                 0.0);
       }
     }
-    {
-      SplitBatch sb(c);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        // the finished block column of L joins the split operand
-        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
-              w, j, j, T);
+    {  // the finished block column of L joins the split operand
+      if (fx) {
+        FSplitBatch sb(c, false);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int w = std::min(p.n, j + nb) - j;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j, j,
+                 p.n - j, w, j, j, p.mx.exL);
+        }
+      } else {
+        SplitBatch sb(c);
+        for (auto &p : P) {
+          const int j = s * nb;
+          if (j >= p.n) continue;
+          const int w = std::min(p.n, j + nb) - j;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
+                 w, j, j, T);
+        }
       }
     }
   }
@@ -1888,7 +1993,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   cd_options opt;
   cd_options_default(&opt);
   if (opt_in) opt = *opt_in;
-  if (opt.nb < 0 || opt.prec < CD_FP64 || opt.prec > CD_MIXED_BF16X6 || opt.out < CD_OUT_TRIL ||
+  if (opt.nb < 0 || opt.prec < CD_FP64 || opt.prec > CD_MIXED_FIXED4 || opt.out < CD_OUT_TRIL ||
       opt.out > CD_OUT_SYM || opt.diag < CD_DIAG_AUTO || opt.diag > CD_DIAG_SYMBOLIC || opt.uplo < CD_LOWER ||
       opt.uplo > CD_UPPER)
     return CD_EINVAL;
@@ -1917,7 +2022,8 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   size_t need = need_bytes(n, batch, nb, opt.prec != CD_FP64, op == OP_DUAL);
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b)
-      need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL);
+      need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL,
+                        opt.prec == CD_MIXED_FIXED4 && factor);
   const bool upper = opt.uplo == CD_UPPER;
   const int narr = 1 + (factor ? 0 : 1) + (op == OP_DUAL ? 1 : 0);  // matrices per problem
   if (upper)
@@ -1979,8 +2085,10 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   }
   if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
   const bool mixed = opt.prec != CD_FP64;
-  if (mixed && (!mixed_available() || !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar)))
-    return CD_ENOMEM;
+  const bool fixed = opt.prec == CD_MIXED_FIXED4 && factor;
+  if (mixed && !mixed_available()) return CD_ECUDA;
+  if (fixed && fixed_init() != CD_OK) return CD_ECUDA;
+  if (mixed && !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar, fixed)) return CD_ENOMEM;
   // The step loops issue the diagonal chain on the high-priority stream (its
   // CTAs are scheduled first when SM slots free up) and the independent bulk
   // GEMM of each step on the side stream; both start after, and the caller's
@@ -2101,6 +2209,7 @@ int cd_create(cd_handle **h, int device) {
     return CD_ECUDA;
   }
   mixed_init();  // on failure only the CD_MIXED_* paths are unavailable
+  fixed_init();
   g_init_done = true;
   if (cudaMalloc(&x->dev_err, sizeof(int)) != cudaSuccess || cudaMemset(x->dev_err, 0, sizeof(int)) != cudaSuccess) {
     free(x);
@@ -2146,7 +2255,8 @@ int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size
   if (!h || !bytes || n_max < 0) return CD_EINVAL;
   const int nb = pick_nb(n_max, opt);
   *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64, true) +
-           ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true) : 0) +
+           ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true,
+                                                      opt->prec == CD_MIXED_FIXED4) : 0) +
            ((opt && opt->uplo == CD_UPPER) ? 3 * (align_up(sizeof(double) * (size_t)n_max * n_max) + kAlign) : 0);
   return CD_OK;
 }
@@ -2258,15 +2368,18 @@ int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {
 
 int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
                         long long ldb, double *C, long long ldc, int prec, int lower, void *stream) {
-  if (!h || M < 0 || N < 0 || K < 1 || (prec != CD_MIXED_BF16X3 && prec != CD_MIXED_BF16X6) || (lower && M != N))
+  if (!h || M < 0 || N < 0 || K < 1 ||
+      (prec != CD_MIXED_BF16X3 && prec != CD_MIXED_BF16X6 && prec != CD_MIXED_FIXED4) || (lower && M != N))
     return CD_EINVAL;
   if (M == 0 || N == 0) return CD_OK;
   if (!A || !B || !C || lda < K || ldb < K || ldc < N) return CD_EINVAL;
   DeviceGuard guard(h->device);
-  if (!mixed_available()) return CD_EINVAL;
-  const int T = mix_terms(prec);
+  const bool fx = prec == CD_MIXED_FIXED4;
+  if (!mixed_available() || (fx && fixed_init() != CD_OK)) return CD_EINVAL;
+  const int T = fx ? kFixedSlices : mix_terms(prec);
   const long long kp = (K + 63) / 64 * 64;
-  const size_t bytes = kPartBytes + 2 * (size_t)T * ((size_t)M * kp + (size_t)N * kp) + 4 * kAlign;
+  const size_t bytes = kPartBytes + 2 * (size_t)T * ((size_t)M * kp + (size_t)N * kp) +
+                       sizeof(int) * ((size_t)M + N) + 6 * kAlign;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ensure_ws(h, bytes, s);
   if (rc) return rc;
@@ -2275,17 +2388,29 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
   ar.cap = h->ws_bytes;
   cd_options opt;
   cd_options_default(&opt);
+  opt.prec = prec;
   Ctx c{h, s, &opt, nullptr, 0, h->gemm_slots};
   c.part = (double *)ar.take(kPartBytes);
   c.part_cap = kPartBytes / sizeof(double);
   void *As = ar.take(2 * (size_t)T * M * kp);
   void *Bs = ar.take(2 * (size_t)T * N * kp);
-  if (!As || !Bs) return CD_ENOMEM;
-  split(c, s, A, lda, M, K, 0, 0, As, kp, M, 0, 0, M, (int)kp, 0, 0, T);
-  split(c, s, B, ldb, N, K, 0, 0, Bs, kp, N, 0, 0, N, (int)kp, 0, 0, T);
+  int *ea = (int *)ar.take(sizeof(int) * M);
+  int *eb = (int *)ar.take(sizeof(int) * N);
+  if (!As || !Bs || !ea || !eb) return CD_ENOMEM;
+  if (fx) {
+    FSplitBatch sb(c, true);
+    sb.add(A, lda, M, K, 0, As, kp, M, 0, 0, M, (int)kp, 0, 0, ea);
+    sb.add(B, ldb, N, K, 0, Bs, kp, N, 0, 0, N, (int)kp, 0, 0, eb);
+  } else {
+    split(c, s, A, lda, M, K, 0, 0, As, kp, M, 0, 0, M, (int)kp, 0, 0, T);
+    split(c, s, B, ldb, N, K, 0, 0, Bs, kp, N, 0, 0, N, (int)kp, 0, 0, T);
+  }
   {
-    MixedBatch mb(c, T, lower != 0);
-    mb.add(mop(As, kp, M, T, 0, 0), mop(Bs, kp, N, T, 0, 0), M, N, K, nullptr, 0, C, ldc, 1.0, 0.0);
+    MixedBatch mb(c, T, lower != 0, false, nullptr, fx);
+    if (fx)
+      mb.add(fop(As, kp, M, ea, 0, 0), fop(Bs, kp, N, eb, 0, 0), M, N, K, nullptr, 0, C, ldc, 1.0, 0.0);
+    else
+      mb.add(mop(As, kp, M, T, 0, 0), mop(Bs, kp, N, T, 0, 0), M, N, K, nullptr, 0, C, ldc, 1.0, 0.0);
   }
   return c.err;
 }

@@ -24,8 +24,9 @@ struct MOp {
   const void *base;
   long long ld;    // elements per row (multiple of 64)
   long long rows;  // rows per term
-  int T;           // terms (2 or 3)
+  int T;           // terms (2 or 3; 4 fixed-point slices for cd_fixed.cu)
   int x0, y0;      // view origin
+  const int *ex;   // fixed-point slices: exponent of each stored row (else unused)
 };
 
 // Cout = beta * Cin + alpha * op(A) op(B)^T over the views (M x K) and (N x K).
@@ -77,8 +78,28 @@ struct SplitArgs {
   int reg_r0, reg_c0, dst_h, dst_w;
   int dst_r0, dst_c0;
   int T;
+  int *ex;  // fixed-point splits: exponent of each destination row (cd_fixed.cu)
 };
 // Independent splits in one launch (count of them).
 cudaError_t mixed_split_group_launch(const SplitArgs *a, int count, cudaStream_t s, int *launches);
+
+// Fixed-point-slice products (cd_fixed.cu, CD_MIXED_FIXED4): operands are
+// MOp views of 4-slice arrays with per-row exponents (MOp::ex); the leading
+// slice products are exact over windows of 512 of K and every window is
+// carried exactly in 64 bits, so each output has one FP64 rounding after
+// the operands' rounding to 2^-32 of their row maxima (13 slice products).  Split-K
+// partials are 64-bit totals (the region holds splits * M * N of them).
+int fixed_init();
+cudaError_t fixed_gemm_launch(const MProblem *probs, int count, bool lower, int *dev_err, cudaStream_t s,
+                              int *launches, int max_units);
+// Fixed-point splits (non-transposed views; SplitArgs::T = 4, ex = exponents
+// of the destination rows): with compute_exponents each row's exponent is
+// first taken from the maximum of its region, otherwise ex is read.
+cudaError_t fixed_split_group_launch(const SplitArgs *a, int count, bool compute_exponents, cudaStream_t s,
+                                     int *launches);
+// ex[i] for the rows of the factor of Sigma (n x n, lds): an exponent E with
+// |L_ik| < 2^E, from |L_ik| <= sqrt(Sigma_ii).  Must run before the
+// factorisation overwrites Sigma.
+cudaError_t fixed_diag_exponents(const double *S, long long lds, int n, int *ex, cudaStream_t s);
 
 }  // namespace cd

@@ -19,7 +19,7 @@ CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_ESCRATCH = 0, -1, -2, -3,
 _ERR = {CD_EINVAL: "invalid argument", CD_ENOMEM: "workspace allocation failed",
         CD_ECUDA: "CUDA error", CD_ETIMEOUT: "device-side wait timed out",
         CD_ESCRATCH: "problem larger than the fixed scratch of cd_chol_rev_noalloc"}
-PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fixed4": 3}
 DIAG = {"auto": 0, "level2": 1, "symbolic": 2}
 OUT = {"tril": 0, "sym": 1}
 
