@@ -158,7 +158,10 @@ struct Ctx {
     cuda(e);
   }
   void cuda(cudaError_t e) {  // after any other CUDA call
-    if (e != cudaSuccess && err == CD_OK) err = CD_ECUDA;
+    if (e != cudaSuccess && err == CD_OK) {
+      err = CD_ECUDA;
+      if (getenv("CD_DEBUG")) fprintf(stderr, "libcholdiff: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+    }
   }
   // Launch through f(), recording an event pair around it when profiling.
   template <class F>

@@ -14,16 +14,16 @@
 //   with b_s = a_s 2^(-8 s) and each a_s an integer in [-128, 128] (exact in
 //   BF16).  Then for C = A B^T (row exponents E_i of A, F_j of B):
 //
-//     C_ij = 2^(E_i + F_j - 14) (acc0 + acc1 + acc2),
-//     acc0 = sum_k b_0 c_0                 integers, |acc0| <= 2^23 per window
-//     acc1 = sum_k (b_0 c_1 + b_1 c_0)     multiples of 2^-8, |acc1| <= 2^16
-//     acc2 = sum_k over s + t in {2, 3, 4} FP32, below 2^-16 of acc0's scale
+//     C_ij = 2^(E_i + F_j - 14) (acc0 + acc1 + acc2 + acc3),
+//     acc0 = sum_k b_0 c_0                 integers, |acc0| <= 2^22 per window
+//     acc1 = sum_k (b_0 c_1 + b_1 c_0)     multiples of 2^-8, below 2^23 of them
+//     acc2 = sum_k over s + t = 2          multiples of 2^-16, below 3 2^22 of them
+//     acc3 = sum_k over s + t in {3, 4}    FP32, below 2^-24 of acc0's scale
 //
-//   over windows of 512 of K, so acc0 and acc1 are exact in FP32 whatever
+//   over windows of 256 of K, so acc0-acc2 are exact in FP32 whatever
 //   the order and rounding of the tensor core's additions (every partial sum
 //   is an integer multiple of the last place below 2^24 units).  Each window
 //   ends with the three accumulators added, exactly, into a 64-bit integer
-//   in units of 2^-32 kept in tensor memory; the last window converts it to
 //   FP64 (one rounding) and forms the output.  Thirteen slice products per
 //   multiply-add (s + t <= 4); error about 2^-32 |A_ik| max|B_j.| +
 //   2^-32 max|A_i.| |B_jk| per term from the operands' rounding, and below
@@ -33,9 +33,9 @@
 //   warp 0   TMA loads of the four slices of A (128 x 64) and B (64 x 64) per
 //            64-wide K block through a two-stage mbarrier ring;
 //   warp 1   tcgen05.mma of the thirteen slice products into one of two
-//            tensor-memory accumulator sets (3 x 64 columns each);
-//   warps 2-9 drain a finished window into the 64-bit total (tensor memory
-//            columns 384-511) and, after the last window, write the output
+//            tensor-memory accumulator sets (4 x 64 columns each);
+//   warps 2-9 add a finished window into their 64-bit totals (registers),
+//            hand the set back and, after the last window, write the output
 //            (or a 64-bit split-K partial).
 // Every wait gives up after 2 s of %globaltimer and reports CD_ETIMEOUT.
 #include <cuda.h>
@@ -57,20 +57,23 @@ using namespace tc;
 
 constexpr int FBM = 128, FBN = 64, FBK = 64;
 constexpr int kSlices = 4;
-constexpr int kWinKb = 8;  // K blocks of one exact window (512 of K)
+constexpr int kWinKb = 4;  // K blocks of one exact window (256 of K)
 constexpr int kStages = 2;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kATile = FBM * FBK * 2;  // one slice of A per K block
 constexpr uint32_t kBTile = FBN * FBK * 2;  // one slice of B per K block
 constexpr uint32_t kStageBytes = kSlices * (kATile + kBTile);
-constexpr int kAccCols = 3 * FBN;   // acc0, acc1, acc2 of one set
-constexpr int kTotCol = 2 * kAccCols;  // 64-bit totals: low words, then high words
+constexpr int kAccs = 4;                // accumulators: s + t = 0, 1, 2 (exact) and 3-4
+constexpr int kAccCols = kAccs * FBN;   // one accumulator set (two sets in tensor memory)
 constexpr int kStageLd = 9;            // FP64 output staging: 32 rows x 8 columns (+1)
 constexpr size_t kEpiBytes = (size_t)kEpiWarps * 32 * kStageLd * sizeof(double);
 constexpr size_t kDynSmem = (size_t)kStages * kStageBytes + kEpiBytes + 1024;
 static_assert(kDynSmem <= 232448 - 1024, "shared memory per CTA");
-static_assert(kTotCol + 2 * FBN <= 512, "tensor memory columns");
+static_assert(2 * kAccCols <= 512, "tensor memory columns");
+// Exact windows: in units of its last place, accumulator d sums (d + 1)
+// products of two integers in [-128, 128] per K: (d + 1) 256 2^14 <= 2^24.
+static_assert((2 + 1) * kWinKb * FBK * (1 << 14) <= (1 << 24), "exact window");
 constexpr int kMaxF = 8;
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
@@ -101,7 +104,7 @@ static_assert(sizeof(FGroup) <= 4096, "kernel parameter block too large");
 
 // round(f 2^32) as a 64-bit integer, from the bits of the binary32 f
 // (integer operations only).  Exact when f is a multiple of 2^-32, which
-// acc0 and acc1 are; acc2 is rounded to the nearest unit (ties away).
+// acc0, acc1 and acc2 are; acc3 is rounded to the nearest unit (ties away).
 // Zeros and subnormals give 0; the shift is clamped for values beyond any
 // reachable accumulator.
 __device__ __forceinline__ long long f32_to_fix(float f) {
@@ -139,26 +142,13 @@ __device__ __forceinline__ double fix_to_f64(long long v, int e2) {
   return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | mant));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // The slice products of one 16-deep K step (s + t <= 4), with their
 // accumulator (0, 1, 2).  Dropping s + t = 4 as well would leave an error of
@@ -175,7 +165,7 @@ __device__ __forceinline__ int prod_b(int q) {
   const int v[kProds] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 3, 2, 1};
   return v[q];
 }
-__device__ __forceinline__ int prod_acc(int q) { return q == 0 ? 0 : q < 3 ? 1 : 2; }
+__device__ __forceinline__ int prod_acc(int q) { return q == 0 ? 0 : q < 3 ? 1 : q < 6 ? 2 : 3; }
 
 struct Unit {
   int p, z, m0, n0, kbeg, nkb;
@@ -221,15 +211,17 @@ __device__ __forceinline__ Unit decode_unit(const FGroup &g, int u) {
 // Windows of a unit: K blocks [w * kWinKb, min(nkb, (w + 1) * kWinKb)).
 __device__ __forceinline__ int windows(int nkb) { return (nkb + kWinKb - 1) / kWinKb; }
 
-template <bool LOWER>
+template <bool LOWER, int COMB>
 __device__ __forceinline__ void epilogue(const FGroup &g, uint32_t tmem, double *stw, int warp, int lane,
                                          volatile int *s_err, uint64_t *tfull_bar, uint64_t *tempty_bar);
 
 // The persistent product.  A window (up to kWinKb K blocks of one unit) is
 // the unit of hand-over between the MMA warp and the epilogue: window t of
 // this CTA (counted over all its units) uses accumulator set t % 2.
-template <bool LOWER>
-__global__ void __maxnreg__(128) k_fgemm(const __grid_constant__ FGroup g) {
+// 168 registers a thread (the epilogue's 32 totals take 64): ten warps put
+// three on some sub-partitions, whose 16K registers then allow 170.
+template <bool LOWER, int COMB>
+__global__ void __maxnreg__(168) k_fgemm(const __grid_constant__ FGroup g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   double *epi = (double *)(smem + (size_t)kStages * kStageBytes);
@@ -337,7 +329,7 @@ __global__ void __maxnreg__(128) k_fgemm(const __grid_constant__ FGroup g) {
                 const uint64_t ad = sw128_desc(sa + prod_a(q) * kATile + kk * 32);
                 const uint64_t bd = sw128_desc(sb + prod_b(q) * kBTile + kk * 32);
                 // the first product of each accumulator in a window overwrites it
-                const bool init = first && kk == 0 && (q == 0 || q == 1 || q == 3);
+                const bool init = first && kk == 0 && (q == 0 || q == 1 || q == 3 || q == 6);
                 mma_bf16_id(acc + (uint32_t)(prod_acc(q) * FBN), ad, bd, kFIdesc, init ? 0u : 1u);
               }
             }
@@ -356,7 +348,7 @@ __global__ void __maxnreg__(128) k_fgemm(const __grid_constant__ FGroup g) {
     }
     __syncwarp();
   } else {
-    epilogue<LOWER>(g, tmem, epi + (size_t)(warp - 2) * 32 * kStageLd, warp, lane, &s_err, tfull_bar, tempty_bar);
+    epilogue<LOWER, COMB>(g, tmem, epi + (size_t)(warp - 2) * 32 * kStageLd, warp, lane, &s_err, tfull_bar, tempty_bar);
   }
   __syncthreads();
   if (warp == 1) {
@@ -388,23 +380,12 @@ __device__ __forceinline__ void write_block8(const FDesc &d, const double *stw, 
   }
 }
 
-template <bool LOWER>
-__device__ __forceinline__ void write_block8_any(const FDesc &d, const double *stw, int rbase, int nrows, int j0,
-                                                 int lane) {
-  switch (d.comb) {
-    case kCopy: write_block8<kCopy, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    case kNeg: write_block8<kNeg, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    case kScale: write_block8<kScale, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    case kAdd: write_block8<kAdd, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    case kSub: write_block8<kSub, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    case kAxpy: write_block8<kAxpy, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-    default: write_block8<kGeneral, LOWER>(d, stw, rbase, nrows, j0, lane); break;
-  }
-}
-
-// Epilogue warp (warps 2-9): tensor-memory lane quarter warp % 4 (32 rows),
-// columns [32 half, 32 half + 32) of the 64-wide tile, 16 at a time.
-template <bool LOWER>
+// Epilogue warp (warps 2-9): tensor-memory lane quarter warp % 4 (32 rows,
+// lane = row) and columns [32 half, 32 half + 32) of the 64-wide tile.  The
+// 64-bit running totals of its 32 elements stay in registers across the
+// unit's windows; each window's four accumulators are added to them and the
+// set is handed back to the MMA warp at once.
+template <bool LOWER, int COMB>
 __device__ __forceinline__ void epilogue(const FGroup &g, uint32_t tmem, double *stw, int warp, int lane,
                                          volatile int *s_err, uint64_t *tfull_bar, uint64_t *tempty_bar) {
   const int qd = warp & 3, half = (warp - 2) / 4;
@@ -415,89 +396,57 @@ __device__ __forceinline__ void epilogue(const FGroup &g, uint32_t tmem, double 
     const FDesc &d = g.d[x.p];
     const int rbase = x.m0 + qd * 32, nrows = max(0, min(32, d.M - rbase));
     const int i = rbase + lane;
-    const int ea = (i < d.M && d.exa) ? d.exa[d.ay + i] : 0;
-    const int nw = windows(x.nkb);
-    for (int w = 0; w < max(nw, 1); ++w) {
-      const bool have = nw > 0;  // a unit with no K block (empty split) writes zeros
+    const int nw = windows(x.nkb);  // 0: an empty split-K part, which writes zeros
+    long long tot[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) tot[q] = 0;
+    for (int w = 0; w < nw; ++w, ++t) {
       const int b = (int)(t & 1u);
-      if (have) {
-        const bool got = mbar_wait_or_abort(&tfull_bar[b], (t >> 1) & 1u, s_err);
-        if (!__all_sync(0xffffffffu, got)) {
-          *s_err = 1;
-          return;
-        }
-        tc_fence_after();
+      const bool got = mbar_wait_or_abort(&tfull_bar[b], (t >> 1) & 1u, s_err);
+      if (!__all_sync(0xffffffffu, got)) {
+        *s_err = 1;
+        return;
       }
-      const bool last = w + 1 >= nw;
-#pragma unroll 1
-      for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
-        long long v[16];
-        if (have) {
-          uint32_t a0[16], a1[16], a2[16];
-          const uint32_t acc = tmem + lane_base + (uint32_t)(b * kAccCols + c0);
-          tmem_ld16(acc, a0);
-          tmem_ld16(acc + FBN, a1);
-          tmem_ld16(acc + 2 * FBN, a2);
+      tc_fence_after();
+      const uint32_t acc = tmem + lane_base + (uint32_t)(b * kAccCols + 32 * half);
+#pragma unroll
+      for (int a = 0; a < kAccs; ++a) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          uint32_t x0[8];
+          tmem_ld8(acc + (uint32_t)(a * FBN + 8 * h), x0);
           tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            v[q] = f32_to_fix(__uint_as_float(a0[q])) + f32_to_fix(__uint_as_float(a1[q])) +
-                   f32_to_fix(__uint_as_float(a2[q]));
-          if (w > 0) {
-            uint32_t lo[16], hi[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)(kTotCol + c0), lo);
-            tmem_ld16(tmem + lane_base + (uint32_t)(kTotCol + FBN + c0), hi);
-            tmem_wait_ld();
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] += (long long)(((unsigned long long)hi[q] << 32) | lo[q]);
-          }
-          if (!last) {
-            uint32_t lo[16], hi[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              lo[q] = (uint32_t)(unsigned long long)v[q];
-              hi[q] = (uint32_t)((unsigned long long)v[q] >> 32);
-            }
-            tmem_st16(tmem + lane_base + (uint32_t)(kTotCol + c0), lo);
-            tmem_st16(tmem + lane_base + (uint32_t)(kTotCol + FBN + c0), hi);
-            tmem_wait_st();
-            continue;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = 0;
-        }
-        // last window: the output of these 16 columns
-        const int j0 = x.n0 + c0;
-        if (d.splits > 1) {
-          if (lane < nrows) {
-            long long *pp = d.part + ((long long)x.z * d.M + i) * d.N;
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (j0 + q < d.N && !(LOWER && j0 + q > i)) pp[j0 + q] = v[q];
-          }
-          continue;
-        }
-        const int jl = j0 + (lane & 15);
-        const int ebl = (jl < d.N && d.exb) ? d.exb[d.by + jl] : 0;
-#pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int eb = __shfl_sync(0xffffffffu, ebl, h8 * 8 + q);
-            stw[lane * kStageLd + q] = fix_to_f64(v[h8 * 8 + q], ea + eb - 46);
-          }
-          __syncwarp();
-          write_block8_any<LOWER>(d, stw, rbase, nrows, j0 + h8 * 8, lane);
-          __syncwarp();
+          for (int q = 0; q < 8; ++q) tot[8 * h + q] += f32_to_fix(__uint_as_float(x0[q]));
         }
       }
-      if (have) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty_bar[b]);
-        ++t;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[b]);
+    }
+    const int j0 = x.n0 + 32 * half;
+    if (d.splits > 1) {
+      if (lane < nrows) {
+        long long *pp = d.part + ((long long)x.z * d.M + i) * d.N;
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (j0 + q < d.N && !(LOWER && j0 + q > i)) pp[j0 + q] = tot[q];
       }
+      continue;
+    }
+    const int ea = (i < d.M) ? d.exa[d.ay + i] : 0;
+    const int jl = j0 + lane;
+    const int ebl = jl < d.N ? d.exb[d.by + jl] : 0;
+#pragma unroll
+    for (int h8 = 0; h8 < 4; ++h8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int eb = __shfl_sync(0xffffffffu, ebl, h8 * 8 + q);
+        stw[lane * kStageLd + q] = fix_to_f64(tot[h8 * 8 + q], ea + eb - 46);
+      }
+      __syncwarp();
+      write_block8<COMB, LOWER>(d, stw, rbase, nrows, j0 + h8 * 8, lane);
+      __syncwarp();
     }
   }
 }
@@ -682,8 +631,11 @@ int fixed_init() {
     return CD_ECUDA;
   }
   g_fencode = (FEncodeFn)fn;
-  cudaError_t e = cudaFuncSetAttribute(k_fgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
-  if (!e) e = cudaFuncSetAttribute(k_fgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+  const int sm = (int)kDynSmem;
+  cudaError_t e = cudaFuncSetAttribute(k_fgemm<false, kCopy>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (!e) e = cudaFuncSetAttribute(k_fgemm<false, kSub>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (!e) e = cudaFuncSetAttribute(k_fgemm<true, kCopy>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (!e) e = cudaFuncSetAttribute(k_fgemm<true, kSub>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   const int carve = cudaSharedmemCarveoutMaxShared;
   if (!e) e = cudaFuncSetAttribute(k_freduce<true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (!e) e = cudaFuncSetAttribute(k_freduce<false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
@@ -722,9 +674,9 @@ cudaError_t fixed_gemm_launch(const MProblem *probs, int count, bool lower, int 
       d.part = reinterpret_cast<long long *>(P.part);  // splits * M * N 8-byte words
       d.exa = P.A.ex;
       d.exb = P.B.ex;
-      d.comb = P.beta == 0.0 ? (P.alpha == 1.0 ? kCopy : P.alpha == -1.0 ? kNeg : kScale)
-               : P.beta == 1.0 ? (P.alpha == 1.0 ? kAdd : P.alpha == -1.0 ? kSub : kAxpy)
-                               : kGeneral;
+      // output modes of the fixed-point product: C = A B^T (copy) or C = Cin - A B^T
+      d.comb = (P.beta == 0.0 && P.alpha == 1.0) ? kCopy : (P.beta == 1.0 && P.alpha == -1.0) ? kSub : -1;
+      if (d.comb < 0 || (g.count > 0 && d.comb != g.d[0].comb)) return cudaErrorInvalidValue;
       d.ldcin = P.ldcin;
       d.ldcout = P.ldcout;
       d.alpha = P.alpha;
@@ -756,10 +708,11 @@ cudaError_t fixed_gemm_launch(const MProblem *probs, int count, bool lower, int 
     if (g.count == 0) continue;
     const int units = g.total_tiles;
     const int grid = std::min(units, std::max(fsm_count(), (units + max_units - 1) / max_units));
+    const int comb = g.d[0].comb;  // one output mode per launch (checked above)
     if (lower)
-      k_fgemm<true><<<grid, kThreads, kDynSmem, s>>>(g);
+      (comb == kCopy ? k_fgemm<true, kCopy> : k_fgemm<true, kSub>)<<<grid, kThreads, kDynSmem, s>>>(g);
     else
-      k_fgemm<false><<<grid, kThreads, kDynSmem, s>>>(g);
+      (comb == kCopy ? k_fgemm<false, kCopy> : k_fgemm<false, kSub>)<<<grid, kThreads, kDynSmem, s>>>(g);
     if (launches) ++*launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
