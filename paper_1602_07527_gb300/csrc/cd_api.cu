@@ -1765,6 +1765,7 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // L_dot into `big2`; D^{-1} is split once per step for both panel solves.
 void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   const int T = P.empty() ? 2 : P[0].mx.T;
+  const bool fx = c.opt->prec == CD_MIXED_FIXED4;  // L's products on fixed-point slices
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
@@ -1773,8 +1774,25 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     k = std::min(p.n, j + nb);
     return j < p.n;
   };
+  if (fx)  // row exponents of L from the diagonal of Sigma, before it is overwritten
+    for (auto &p : P)
+      c.launch("diag_exponents", 0.0, 12.0 * p.n,
+               [&] { return fixed_diag_exponents(p.X, p.ldx, p.n, p.mx.exL, c.s); });
+  const auto fL = [&](const Prob &p, int x0, int y0) {
+    return fop(p.mx.fbig, (p.n + 63) / 64 * 64, p.n, p.mx.exL, x0, y0);
+  };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     c.fork();
+    if (fx) {  // f1 on fixed-point slices
+      MixedBatch mb(c, T, true, false, "f1", true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j;
+        double *D = p.X + (long long)j * p.ldx + j;
+        mb.add(fL(p, 0, j), fL(p, 0, j), w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
+      }
+    }
     {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T).
        // f1 and g1 are enqueued before the side stream's f3 and g3, so that their CTAs take SMs first.
       MixedBatch mb(c, T, true, false, "f1+g1");
@@ -1784,7 +1802,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int w = k - j;
         double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
         const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
-        mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        if (!fx) mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
         mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), R, w, w, j, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
       }
     }
@@ -1799,6 +1817,16 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
                Dd, p.ldxd, -1.0, 1.0);
       }
     }
+    if (fx) {  // f3 on fixed-point slices (side stream)
+      MixedBatch mb(c, T, false, true, "f3", true);
+      for (auto &p : P) {
+        int j, k;
+        if (!blk(p, s, j, k)) continue;
+        const int w = k - j, m = p.n - k;
+        double *C = p.X + (long long)k * p.ldx + j;
+        mb.add(fL(p, 0, k), fL(p, 0, j), m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
+      }
+    }
     {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
       MixedBatch mb(c, T, false, true, "f3+g3");
       for (auto &p : P) {
@@ -1807,7 +1835,7 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int w = k - j, m = p.n - k;
         double *C = p.X + (long long)k * p.ldx + j, *Cd = p.Xd + (long long)k * p.ldxd + j;
         const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), R, m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
+        if (!fx) mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), R, m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
         mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, k), R, m, w, j, Cd, p.ldxd, Cd, p.ldxd, -1.0, 1.0);
       }
     }
@@ -1875,19 +1903,34 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           if (!blk(p, s, j, k)) continue;
           const int w = k - j, m = p.n - k;
           if (m <= 0) continue;
-          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          if (!fx) sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
           sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
           sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, w, w, 1, 0, p.mx.P3, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false, false, "f4");
+      if (fx) {
+        FSplitBatch fb(c, true);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k)) continue;
+          const int w = k - j, m = p.n - k;
+          if (m <= 0) continue;
+          fb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, p.mx.fP1, nb, p.n, 0, 0, m, nb, 0, 0, p.mx.exP1);
+          fb.add(p.dinv, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
+        }
+      }
+      MixedBatch mb(c, T, false, false, "f4", fx);
       for (auto &p : P) {
         int j, k;
         if (!blk(p, s, j, k)) continue;
         const int w = k - j, m = p.n - k;
         double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
-               0.0);
+        if (fx)
+          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, 0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), m, w, w, nullptr, 0,
+                 Cb, p.ldx, 1.0, 0.0);
+        else
+          mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
+                 0.0);
       }
     }
     {  // the finished block column of L joins the split operand
@@ -1898,6 +1941,16 @@ void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int w = k - j, m = p.n - k;
         sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j, w, j,
                j, T);
+      }
+      if (fx) {  // and its fixed-point slices for L's own products
+        FSplitBatch fb(c, false);
+        for (auto &p : P) {
+          int j, k;
+          if (!blk(p, s, j, k)) continue;
+          const int w = k - j;
+          fb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j, j,
+                 p.n - j, w, j, j, p.mx.exL);
+        }
       }
     }
     {  // g4a: C_dot <- C_dot - C D_dot^T
