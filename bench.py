@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dual", action="store_true", help="skip the one-loop chol_fwd_and_sens leg")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the served Poisson stream")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the FP64 block-size sweep (N 4096/8192, nb 64-256)")
+    ap.add_argument("--no-peak", action="store_true", help="skip the FP64 peak probes")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served Poisson stream")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-lanes", type=int, default=2)
     ap.add_argument("--serve-sustained-rate", type=float, default=250.0,
@@ -295,7 +297,12 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": ours_config(args),
+        # the metric's workload (ours_config) sampled at N = ref_n: the oracle's
+        # O(N^3) scalar loop would take minutes per step at the full N
+        "config": dict(ours_config(args), workload=(
+            f"chol_rev FP64, SE covariance ell 0.3 on [0,1]^3 + 1e-4 I (seed {SE_SEED}): oracle sample at "
+            f"N={n} per step (our arm's N={args.n}); throughput scales the sample by 2N^3/3"), n=n,
+            sample_of_n=args.n),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: one oracle chol_unblocked_rev at N={n} (same SE recipe)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -310,6 +317,73 @@ def ours_config(args):
             "step": "chol_fwd -> chol_fwd_sens -> chol_rev on one N x N problem",
             "l2": "inputs exceed L2 (512 MiB per FP64 matrix at N=8192); no flush",
             "parallelism": "replicas (one independent problem per GPU)"}
+
+
+def fp64_peak_leg(dev):
+    """The FP64 pipe's rate on this GPU: register-only DFMA chains (the
+    instruction of the library's FP64 products) and the FP64 matrix
+    instruction (mma.sync m8n8k4), each timed with CUDA events."""
+    import torch
+    from paper_1602_07527_gb300 import native as nat
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for kind in ("dfma", "dmma"):
+        nat.fp64_probe(kind, 20000, dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = nat.fp64_probe(kind, 400000, dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[kind + "_tflops"] = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    out["derived_dfma_tflops"] = FP64_PEAK_TFLOPS
+    out["how"] = ("4 CTAs x 256 threads per SM, register operands only: 8 independent FMA chains a thread "
+                  "(dfma) or 4 chains of mma.sync m8n8k4 f64 a thread (dmma); CUDA events")
+    return out
+
+
+def nb_sweep_leg(args, dev):
+    """Block size sweep of the large FP64 configuration: SE covariance (ell 0.3
+    on [0,1]^3 + 1e-4 I), N in {4096, 8192}, nb in {64, 128, 256}; median of
+    three CUDA-event-timed calls after one warm-up, inputs restored outside the
+    timed region."""
+    import torch
+    import paper_1602_07527_gb300 as cd
+    from paper_1602_07527_gb300 import workloads as W
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in (4096, 8192):
+        S, Lb = W.large_se_case(n, SE_SEED)
+        S0 = torch.tensor(np.tril(S), device=dev)
+        Lb0 = torch.tensor(Lb, device=dev)
+        del S, Lb
+        L = S0.clone()
+        cd.chol_fwd(L)
+        X = torch.empty_like(S0)
+        for nb in (64, 128, 256):
+            t = {}
+            for op in ("chol_fwd", "chol_rev"):
+                ms = []
+                for r in range(4):
+                    X.copy_(S0 if op == "chol_fwd" else Lb0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if op == "chol_fwd":
+                        cd.chol_fwd(X, nb=nb)
+                    else:
+                        cd.chol_rev(L, X, nb=nb)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if r:
+                        ms.append(e0.elapsed_time(e1))
+                m = statistics.median(ms)
+                fl = flops_fwd(n) if op == "chol_fwd" else flops_rev(n)
+                t[op] = {"ms": m, "tflops": fl / (m * 1e-3) / 1e12}
+            rows.append({"n": n, "nb": nb, **t})
+        del S0, Lb0, L, X
+        torch.cuda.empty_cache()
+    return rows
 
 
 # ---------------------------------------------------------------------------
@@ -355,7 +429,6 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     cd.profile_read(dev)  # discard warm-up records
-    cd.profile_enable(True, dev)
     clocks = ClockSampler(d.local)
     d.barrier()
     torch.cuda.synchronize()
@@ -372,9 +445,19 @@ def run_ours(args):
     d.barrier()
     clock_info = clocks.stop()
     launches = cd.launch_count(dev) - launches0
+    total_ms = d.max(t0.elapsed_time(t1))
+    # the per-kernel profile (an event pair around every launch) from one more
+    # step after the timed ones, so that its events do not slow the timed steps
+    cd.profile_enable(True, dev)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    step()
+    p1.record(stream)
+    torch.cuda.synchronize()
     kstats = cd.profile_read(dev)
     cd.profile_enable(False, dev)
-    total_ms = d.max(t0.elapsed_time(t1))
+    prof_ms = p0.elapsed_time(p1)
     op_ms = {"chol_fwd": [], "chol_fwd_sens": [], "chol_rev": []}
     for ev, info in evs:
         op_ms["chol_fwd"].append(ev[0].elapsed_time(ev[1]))
@@ -415,7 +498,13 @@ def run_ours(args):
         dual = {"ms_median": dm, "tflops": (flops_fwd(n) + flops_sens(n)) / (dm * 1e-3) / 1e12,
                 "separate_ms": sep, "speedup_vs_separate": sep / dm}
 
-    # roofline of the dominant kernel (largest total device time in the timed region)
+    peak = None if args.no_peak else fp64_peak_leg(dev)
+    fp64_peak = peak["dfma_tflops"] if peak else FP64_PEAK_TFLOPS
+    # executed work of the profiled step (the library's per-launch algorithmic
+    # flops, all terms) beside the nominal N^3/3 + 2 N^3/3 + 2 N^3/3
+    flops_exec = {"executed_step": sum(k["flops"] for k in kstats),
+                  "nominal_step": flops_fwd(n) + flops_sens(n) + flops_rev(n)}
+    # roofline of the dominant kernel (largest total device time in the profiled step)
     dom = kstats[0] if kstats else None
     roofline = None
     if dom:
@@ -425,15 +514,19 @@ def run_ours(args):
         traffic = None
         if dom["name"] == "gemm_f64<N,T>" and dom["launches"] > 0:
             traffic = GEMM_NT_DRAM_BYTES_PER_FLOP * dom["flops"] / dom["launches"]
-        roofline = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        roofline = {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                     "traffic_source": ("ncu at N=4096 (two launches: 28.0 MB in 0.734 GFLOP), scaled by the "
                                        "launch's flops" if traffic is not None else None),
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 pipe)",
+                    "peak_source": ("measured in this run: DFMA chains on every SM (fp64_peak.dfma_tflops), "
+                                    "of measured" if peak else
+                                    "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (FP64 pipe)"),
+                    "frac_of_derived_pipe": achieved / FP64_PEAK_TFLOPS,
                     "launches": dom["launches"], "ms_per_launch": dom["ms"] / max(1, dom["launches"]),
-                    "share_of_timed_region": dom["ms"] / (t0.elapsed_time(t1))}
+                    "share_of_profiled_step": dom["ms"] / prof_ms,
+                    "measured_over": "one profiled step after the timed steps (CUDA events on the kernel's stream)"}
     kernels = [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 3),
-                "share": k["ms"] / t0.elapsed_time(t1),
+                "share": k["ms"] / prof_ms,
                 "tflops": (k["flops"] / (k["ms"] * 1e-3) / 1e12) if k["ms"] > 0 else 0.0}
                for k in kstats[:8]]
 
@@ -454,7 +547,7 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize()
-        ks = max(1, min(args.steps, 3))
+        ks = max(1, args.steps)
         d.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -484,7 +577,7 @@ def run_ours(args):
         ref_L, ref_Ld, ref_Sb = A.clone(), Ad.clone(), Ab.clone()
         Lexact = A.clone()
         mixed = {"workload": f"Matern-5/2 ell 0.2 on [0,1]^4 + 1e-3 I, N={n} (seed 3); errors vs the FP64 path"}
-        for prec in ("bf16x6", "bf16x3"):
+        for prec in ("fixed4", "bf16x6", "bf16x3"):
             for _ in range(max(1, args.warmup - 1)):
                 step(prec)
             torch.cuda.synchronize()
@@ -506,11 +599,15 @@ def run_ours(args):
             Ab.copy_(Lb0)
             cd.chol_rev(Lexact, Ab, nb=nb, prec=prec)
             e["Sigma_bar_given_fp64_L"] = rel(Ab, ref_Sb)
+            Ad.copy_(Sd0)
+            cd.chol_fwd_sens(Lexact, Ad, nb=nb, prec=prec)
+            e["L_dot_given_fp64_L"] = rel(Ad, ref_Ld)
+            e["max"] = max(e.values())
             if not args.no_dual:
                 dms = time_dual(prec)
                 entry_dual = {"ms": dms, "separate_ms": mfwd + msens, "speedup_vs_separate": (mfwd + msens) / dms,
                               "rel_err_vs_fp64": {"L": rel(A, ref_L), "L_dot": rel(Ad, ref_Ld)}}
-            tk = next((k for k in mk if k["name"].startswith("mgemm")), None)
+            tk = next((k for k in mk if k["name"].startswith(("mgemm", "fgemm"))), None)
             entry = {"chol_rev_tflops": d.ws * flops_rev(n) / (d.max(mrev) * 1e-3) / 1e12,
                      "chol_fwd_tflops": flops_fwd(n) / (mfwd * 1e-3) / 1e12,
                      "chol_fwd_sens_tflops": flops_sens(n) / (msens * 1e-3) / 1e12,
@@ -529,6 +626,13 @@ def run_ours(args):
                 entry["fwd_and_sens"] = entry_dual
             mixed[prec] = entry
 
+    sweep = None
+    if not args.no_sweep:
+        del A, Ab, Ad
+        torch.cuda.empty_cache()
+        sweep = nb_sweep_leg(args, dev)
+        A, Ab, Ad = torch.empty_like(S0), torch.empty_like(Lb0), torch.empty_like(Sd0)
+
     serving = None
     if not args.no_serving:
         del A, Ab, Ad, S0, Lb0, Sd0
@@ -545,7 +649,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: SE covariance (ell 0.3, points U[0,1]^3, jitter 1e-4), L_bar and Sigma_dot iid N(0,1)",
         "config": ours_config(args), "ops": ops, "roofline": roofline, "kernels": kernels,
-        "fwd_and_sens": dual, "mixed": mixed, "serving": serving,
+        "fwd_and_sens": dual, "mixed": mixed, "serving": serving, "nb_sweep": sweep, "fp64_peak": peak,
+        "flops": flops_exec,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clock_info,
         "step_tflops": d.ws * (flops_fwd(n) + flops_sens(n) + flops_rev(n)) / (total_ms / args.steps * 1e-3) / 1e12,
     }
@@ -564,7 +669,12 @@ def serve_bench(args, dev):
     from paper_1602_07527_gb300 import workloads as W
     stream = W.serving_stream(seed=5, rate=args.serve_rate, duration=args.serve_seconds)
     reqs = sv.requests_from_stream(stream, mixed_prec="bf16x6")
-    sv.prepare(reqs, dev)  # payloads resident in HBM before the replay starts
+    # the full stream's inputs (about 28 MB a request) do not all fit in HBM at
+    # once: each request's inputs are drawn on the device from its seed when its
+    # batch is launched (about 0.1 ms of device time against a solve of 1-60 ms)
+    prepared = sum(sv.request_bytes(r.n, r.prec) for r in reqs) <= 100e9
+    if prepared:
+        sv.prepare(reqs, dev)  # payloads resident in HBM before the replay starts
     # warm the lanes (workspace growth, first-launch costs) on a few requests
     warm = sv.Server(dev, mem_cap=40e9, lanes_per_prec=args.serve_lanes, precisions=("fp64", "bf16x6"))
     warm.run(sv.requests_from_stream(W.serving_stream(seed=6, rate=2000.0, duration=0.01)), realtime=False)
@@ -576,9 +686,9 @@ def serve_bench(args, dev):
     wall = time.perf_counter() - t0
     offered = sv.summarize(done, wall)
     by_prec = {p: sv.summarize([r for r in done if r.prec == p], wall) for p in ("fp64", "bf16x6")}
-    # the same kinds of requests alone: a sample of 40, one at a time on the idle GPU
+    # the same kinds of requests alone: a sample of 1000, one at a time on the idle GPU
     rng = np.random.default_rng(7)
-    sample = [reqs[i] for i in sorted(rng.choice(len(reqs), size=min(40, len(reqs)), replace=False))]
+    sample = [reqs[i] for i in sorted(rng.choice(len(reqs), size=min(1000, len(reqs)), replace=False))]
     alone = []
     for r in sample:
         r.payload = sv.build_inputs(r, dev)
@@ -587,12 +697,13 @@ def serve_bench(args, dev):
         sv.solve_alone(r, dev)
         torch.cuda.synchronize()
         alone.append(time.perf_counter() - t)
+        r.payload = None
     served_sample = [r.t_done - r.t_admit for r in done if r.rid in {q.rid for q in sample}]
     for r in reqs:
         r.payload = None
     torch.cuda.empty_cache()
     # the same mix at a rate the GPU sustains: queueing no longer dominates
-    sus_stream = W.serving_stream(seed=8, rate=args.serve_sustained_rate, duration=2.0)
+    sus_stream = W.serving_stream(seed=8, rate=args.serve_sustained_rate, duration=args.serve_seconds)
     sus_reqs = sv.requests_from_stream(sus_stream, mixed_prec="bf16x6")
     sv.prepare(sus_reqs, dev)
     t1 = time.perf_counter()
@@ -606,12 +717,14 @@ def serve_bench(args, dev):
     server.close()
     mean_n3 = float(np.mean([r.n ** 3 for r in reqs]))
     return {"stream": (f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, N log-uniform [32, 4096], "
-                       "payloads resident in HBM before the replay, "
+                       + ("payloads resident in HBM before the replay, " if prepared else
+                          "payloads drawn on the device from each request's seed at launch, ") +
                        f"50/50 FP64 / split-BF16 x6, SE ell 0.3 on [0,1]^3 + {sv.SE_JITTER:g} I, 40 GB budget, "
                        f"{args.serve_lanes} lanes per precision"),
             "offered_tflops": args.serve_rate * mean_n3 / 1e12,
             "served": offered, "served_by_precision": by_prec, "sustained": sustained,
-            "peak_bytes": server.peak_bytes,
+            "peak_bytes": server.peak_bytes, "lane_workspace_bytes": server.ws_total,
+            "admission": "HBM budget = the lanes' reserved workspaces + the buffers of requests in flight",
             "host_launch_s": server.host_launch_s, "host_phase_s": server.host_phase_s,
             "alone_sample": {"requests": len(alone), "p50_ms": 1e3 * sv.percentile(alone, 50),
                              "p99_ms": 1e3 * sv.percentile(alone, 99),

@@ -148,8 +148,20 @@ void cd_options_default(cd_options *opt);
  * allocating. */
 int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size_t *bytes);
 
-/* Grow the handle's workspace to at least `bytes` now (returns when it is allocated). */
+/* Bytes of workspace any batched call over the `batch` problem sizes n[]
+ * (host array) with these options may use: the bound the handle's workspace
+ * grows to for that batch.  A caller that keeps a handle's workspace at a
+ * fixed size (cd_reserve) and admits only batches whose bound fits keeps the
+ * library from allocating during its calls. */
+int cd_workspace_size_batched(const cd_handle *h, int batch, const int *n, const cd_options *opt, size_t *bytes);
+
+/* Grow the handle's workspace to `bytes` now if it holds less (exactly that
+ * many bytes; returns when it is allocated).  Growth inside the compute calls
+ * adds an eighth as headroom. */
 int cd_reserve(cd_handle *h, size_t bytes);
+
+/* Bytes of workspace the handle holds now. */
+int cd_workspace_bytes(const cd_handle *h, size_t *bytes);
 
 /*
  * Blocked Cholesky factorisation (Sec. 4.2 chol_blocked, mirroring DPOTRF):
@@ -276,6 +288,17 @@ int cd_chol_rev_noalloc(int n, const double *L, long long ldl, double *Abar, lon
  */
 int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long long lda, const double *B,
                         long long ldb, double *C, long long ldc, int prec, int lower, void *stream);
+
+/*
+ * Measurement support (no counterpart in the paper): the rate of the FP64
+ * pipe.  Launches 4 CTAs of 256 threads per SM, each thread running `iters`
+ * rounds of register-only FP64 work: kind 0 eight independent FMA chains
+ * (DFMA, the instruction of the FP64 products here), kind 1 four chains of
+ * the FP64 matrix instruction mma.sync m8n8k4 (DMMA).  *flops receives the
+ * floating-point operations launched (2 per multiply-add); the caller times
+ * the launch on `stream`.  Returns CD_EINVAL for a bad kind or iters < 1.
+ */
+int cd_debug_fp64_probe(cd_handle *h, int kind, long long iters, void *stream, double *flops);
 
 /*
  * Scheduling knob (no counterpart in the paper).  Every call runs its

@@ -2024,14 +2024,14 @@ size_t need_bytes(const int *n, int batch, int nb, bool mixed = false, bool dual
 // work already enqueued on `s` (which every earlier call of this handle has
 // joined back into) and the new one is usable by work enqueued after it, so
 // growing never waits for the device.
-int ensure_ws(cd_handle *h, size_t bytes, cudaStream_t s) {
+int ensure_ws(cd_handle *h, size_t bytes, cudaStream_t s, bool headroom = true) {
   if (bytes <= h->ws_bytes) return CD_OK;
   if (h->ws) {
     cudaFreeAsync(h->ws, s);
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
-  bytes = bytes + bytes / 8;  // headroom: fewer regrowths for slowly growing batches
+  if (headroom) bytes = bytes + bytes / 8;  // fewer regrowths for slowly growing batches
   if (cudaMallocAsync(&h->ws, bytes, s) != cudaSuccess) {
     cudaGetLastError();
     h->ws = nullptr;
@@ -2317,10 +2317,34 @@ int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size
   return CD_OK;
 }
 
+int cd_workspace_size_batched(const cd_handle *h, int batch, const int *n, const cd_options *opt, size_t *bytes) {
+  if (!h || !bytes || batch < 0 || (batch > 0 && !n)) return CD_EINVAL;
+  int nmax = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] < 0) return CD_EINVAL;
+    nmax = std::max(nmax, n[b]);
+  }
+  const int nb = pick_nb(nmax, opt);
+  const bool mixed = opt && opt->prec != CD_FP64;
+  size_t need = need_bytes(n, batch, nb, mixed, true);
+  for (int b = 0; b < batch; ++b) {
+    if (mixed) need += mix_bytes(n[b], nb, mix_terms(opt->prec), true, opt->prec == CD_MIXED_FIXED4);
+    if (opt && opt->uplo == CD_UPPER) need += 3 * (align_up(sizeof(double) * (size_t)n[b] * n[b]) + kAlign);
+  }
+  *bytes = need;
+  return CD_OK;
+}
+
+int cd_workspace_bytes(const cd_handle *h, size_t *bytes) {
+  if (!h || !bytes) return CD_EINVAL;
+  *bytes = h->ws_bytes;
+  return CD_OK;
+}
+
 int cd_reserve(cd_handle *h, size_t bytes) {
   if (!h) return CD_EINVAL;
   DeviceGuard guard(h->device);
-  const int rc = ensure_ws(h, bytes, nullptr);
+  const int rc = ensure_ws(h, bytes, nullptr, false);  // exactly what the caller reserves
   if (rc == CD_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) return CD_ECUDA;
   return rc;
 }
@@ -2400,6 +2424,14 @@ int cd_chol_jacobian(cd_handle *h, int n, const double *L, long long ldl, double
   const double n4 = (double)n * n * n * n;
   c.launch("jacobian", 4.0 * n4, 8.0 * n4, [&] { return launch_jacobian(n, L, ldl, Li, n, S, J, s); });
   return c.err;
+}
+
+int cd_debug_fp64_probe(cd_handle *h, int kind, long long iters, void *stream, double *flops) {
+  if (!h || (kind != 0 && kind != 1) || iters < 1 || !flops) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  const cudaError_t e = launch_fp64_probe(kind, 4 * h->num_sms, iters, (cudaStream_t)stream, flops);
+  ++h->launches;
+  return e == cudaSuccess ? CD_OK : CD_ECUDA;
 }
 
 int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {

@@ -1047,4 +1047,57 @@ cudaError_t tile_kernels_init() {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 peak probes (measurement support): the rate of the FP64 pipe as the
+// products above use it (DFMA) and of the FP64 matrix instruction
+// (mma.sync m8n8k4), on register operands only.  Eight independent chains a
+// thread hide the pipe's latency; the sink store never happens for the
+// values reached, but the compiler cannot know that.
+__device__ double g_fp64_sink;
+
+__global__ void __launch_bounds__(256) k_dfma_probe(long long iters, double seed) {
+  double a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = seed * (threadIdx.x + c + 1);
+  const double x = 1.0 - 1e-12, y = 1e-15;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], x, y);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  if (s == 1234.5678) g_fp64_sink = s;
+}
+
+__global__ void __launch_bounds__(256) k_dmma_probe(long long iters, double seed) {
+  double d[4][2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) d[c][0] = d[c][1] = seed * (threadIdx.x + c);
+  const double a = 1.0 - 1e-12, b = 1e-3;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(d[c][0]), "+d"(d[c][1])
+                   : "d"(a), "d"(b));
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s += d[c][0] + d[c][1];
+  if (s == 1234.5678) g_fp64_sink = s;
+}
+
+cudaError_t launch_fp64_probe(int kind, int blocks, long long iters, cudaStream_t st, double *flops) {
+  const int threads = 256;
+  if (kind == 0) {
+    k_dfma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
+    *flops = 2.0 * 8.0 * (double)iters * threads * blocks;
+  } else {
+    k_dmma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
+    *flops = 2.0 * 256.0 * 4.0 * (double)iters * (threads / 32) * blocks;  // 8 x 8 x 4 per warp instruction
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace cd

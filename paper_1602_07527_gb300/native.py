@@ -73,6 +73,8 @@ def lib():
         L.cd_options_default.restype = None
         L.cd_workspace_size.argtypes = [_vp, _i, P(Options), P(ctypes.c_size_t)]
         L.cd_reserve.argtypes = [_vp, ctypes.c_size_t]
+        L.cd_workspace_size_batched.argtypes = [_vp, _i, _vp, P(Options), P(ctypes.c_size_t)]
+        L.cd_workspace_bytes.argtypes = [_vp, P(ctypes.c_size_t)]
         L.cd_chol_fwd.argtypes = [_vp, _i, _vp, _ll, P(Options), _vp, _vp]
         L.cd_chol_rev.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp]
         L.cd_chol_fwd_sens.argtypes = [_vp, _i, _vp, _ll, _vp, _ll, P(Options), _vp]
@@ -83,6 +85,7 @@ def lib():
         L.cd_chol_fwd_and_sens_batched.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp, P(Options), _vp, _vp]
         L.cd_chol_jacobian.argtypes = [_vp, _i, _vp, _ll, _vp, _vp]
         L.cd_get_last_device_error.argtypes = [_vp, P(_i)]
+        L.cd_debug_fp64_probe.argtypes = [_vp, _i, _ll, _vp, P(ctypes.c_double)]
         L.cd_launch_count.argtypes = [_vp]
         L.cd_launch_count.restype = _ll
         L.cd_version.restype = ctypes.c_char_p
@@ -104,7 +107,8 @@ def exported_symbols():
             "cd_chol_rev_batched", "cd_chol_fwd_sens_batched", "cd_get_last_device_error",
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read", "cd_profile_timeline",
             "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout",
-            "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched", "cd_chol_jacobian"]
+            "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched", "cd_chol_jacobian", "cd_debug_fp64_probe",
+            "cd_workspace_size_batched", "cd_workspace_bytes"]
 
 
 def handle(device=None):
@@ -349,6 +353,16 @@ def mixed_gemm_debug(A, B, C, prec="bf16x3", lower=False):
     return C
 
 
+def fp64_probe(kind="dfma", iters=200000, device=None):
+    """Launch the FP64 peak probe (kind "dfma" or "dmma") on the current stream;
+    returns the floating-point operations it performs."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    fl = ctypes.c_double(0.0)
+    _check(lib().cd_debug_fp64_probe(handle(dev), 0 if kind == "dfma" else 1, ctypes.c_longlong(iters), _stream(dev),
+                                     ctypes.byref(fl)), "cd_debug_fp64_probe")
+    return fl.value
+
+
 def launch_count(device=None, handle_=None):
     return int(lib().cd_launch_count(_h(handle_, device)))
 
@@ -379,8 +393,29 @@ def workspace_size(n, nb=0, prec="fp64", device=None, uplo="lower"):
     return out.value
 
 
-def reserve(nbytes, device=None):
-    _check(lib().cd_reserve(handle(device), int(nbytes)), "cd_reserve")
+def workspace_size_batched(ns, nb=0, prec="fp64", handle_=None, device=None):
+    """Workspace bytes a batched call over the problem sizes ns may use (host arithmetic)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    arr = (ctypes.c_int * max(1, len(ns)))(*[int(x) for x in ns])
+    o = options(nb, prec)
+    b = ctypes.c_size_t(0)
+    _check(lib().cd_workspace_size_batched(_h(handle_, dev), len(ns), ctypes.cast(arr, _vp), ctypes.byref(o),
+                                           ctypes.byref(b)), "cd_workspace_size_batched")
+    return b.value
+
+
+def workspace_bytes(handle_=None, device=None):
+    """Bytes of workspace the handle holds now."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    b = ctypes.c_size_t(0)
+    _check(lib().cd_workspace_bytes(_h(handle_, dev), ctypes.byref(b)), "cd_workspace_bytes")
+    return b.value
+
+
+def reserve(nbytes, device=None, handle_=None):
+    """Grow the handle's workspace to at least nbytes now."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _check(lib().cd_reserve(_h(handle_, dev), int(nbytes)), "cd_reserve")
 
 
 def profile_enable(on=True, device=None):

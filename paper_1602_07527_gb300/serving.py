@@ -13,6 +13,12 @@ together inside the same grouped kernels (cd_chol_*_batched), and the
 batches of all lanes overlap on the device.  Sub-batches complete through
 their own CUDA events; their memory then returns to the budget and newly
 arrived requests are admitted.
+
+The HBM budget covers everything the server holds on the device: each lane's
+library workspace, reserved once when the server starts (the library then
+never allocates during a call, because a batch is admitted to a lane only if
+the workspace bound of its sizes, cd_workspace_size_batched, fits that
+reservation), plus the buffers of the requests in flight.
 """
 import collections
 import dataclasses
@@ -52,11 +58,15 @@ def requests_from_stream(stream, mixed_prec="bf16x6"):
 
 def request_bytes(n: int, prec: str) -> int:
     """HBM held by one request in flight: its Sigma/L and L_bar/Sigma_bar
-    buffers, plus the split-BF16 operand copies of a mixed request."""
-    b = 2 * n * n * 8
-    if prec != "fp64":
-        b += (3 if prec == "bf16x6" else 2) * 2 * 2 * n * (n + 72)
-    return b
+    buffers (the split-BF16 operand copies of a mixed request live in the
+    lane's workspace, counted separately)."""
+    return 2 * n * n * 8
+
+
+def lane_workspace_bytes(device, prec, nb=0, n_max=4096, ws_requests=2) -> int:
+    """The workspace one lane of precision `prec` reserves: the library's
+    bound for a batched call over ws_requests problems of size n_max."""
+    return native.workspace_size_batched([int(n_max)] * int(ws_requests), nb=nb, prec=prec, device=device)
 
 
 def build_inputs(req: Request, device, ell=SE_ELL, jitter=SE_JITTER):
@@ -94,14 +104,17 @@ class _Lane:
     library's host loop runs without holding the GIL), so lanes enqueue work
     in parallel while the scheduler thread keeps admitting and completing."""
 
-    def __init__(self, device, prec, high):
+    def __init__(self, device, prec, high, ws_bytes, nb):
         self.device = device
         self.prec = prec
+        self.nb = nb
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -5)
         self.stream = torch.cuda.Stream(device, priority=hi if high else 0)
         self.handle = native.Handle(device)
         # cheap (split-BF16) requests are scheduled ahead of FP64 ones on a shared GPU
         self.handle.set_priorities(hi if high else min(0, hi + 2), hi + 1 if high else 0)
+        native.reserve(ws_bytes, device, handle_=self.handle)   # held for the server's life
+        self.ws_bytes = native.workspace_bytes(self.handle, device)
         self.inflight = collections.deque()   # (event, requests, bytes, last), in stream order
         self.lock = threading.Lock()
         self.batches = 0                      # admitted batches not yet complete (scheduler thread only)
@@ -141,14 +154,21 @@ class Server:
     """
 
     def __init__(self, device="cuda:0", mem_cap=40e9, lanes_per_prec=2, max_batch=64, nb=0, depth=2,
-                 keep_results=False, precisions=("fp64", "bf16x6", "bf16x3")):
+                 keep_results=False, precisions=("fp64", "bf16x6", "bf16x3"), n_max=4096, ws_requests=2):
         self.device = torch.device(device)
         self.mem_cap = float(mem_cap)
         self.max_batch = int(max_batch)
         self.nb = nb
         self.depth = int(depth)
         self.keep = keep_results
-        self.lanes = [_Lane(self.device, p, p != "fp64") for p in precisions for _ in range(lanes_per_prec)]
+        self.n_max = int(n_max)
+        # each lane's workspace: the bound for ws_requests problems of the largest size
+        ws = {p: lane_workspace_bytes(self.device, p, nb, self.n_max, ws_requests) for p in precisions}
+        self.lanes = [_Lane(self.device, p, p != "fp64", ws[p], nb) for p in precisions
+                      for _ in range(lanes_per_prec)]
+        self.ws_total = float(sum(ln.ws_bytes for ln in self.lanes))
+        if self.ws_total >= self.mem_cap:
+            raise ValueError("the lanes' workspaces alone exceed the memory cap")
         self.peak_bytes = 0.0
 
     @property
@@ -162,6 +182,10 @@ class Server:
     def close(self):
         for ln in self.lanes:
             ln.close()
+
+    def _ws_need(self, ns, prec):
+        """Workspace bound of one batched call over sizes ns (host arithmetic)."""
+        return native.workspace_size_batched(ns, nb=self.nb, prec=prec, device=self.device)
 
     def _launch(self, lane: _Lane, batch: List[Request]):
         """Enqueue one admitted batch on the lane (lane thread); returns its entries."""
@@ -200,14 +224,17 @@ class Server:
         list of completed requests with t_admit / t_done filled in."""
         reqs = sorted(requests, key=lambda r: r.t_arrival)
         precs = {ln.prec for ln in self.lanes}
+        lane_ws = {ln.prec: ln.ws_bytes for ln in self.lanes}
         for r in reqs:
-            if request_bytes(r.n, r.prec) > self.mem_cap:
+            if request_bytes(r.n, r.prec) > self.mem_cap - self.ws_total:
                 raise ValueError(f"request {r.rid} alone exceeds the memory cap")
+            if r.prec in lane_ws and self._ws_need([r.n], r.prec) > lane_ws[r.prec]:
+                raise ValueError(f"request {r.rid} needs more workspace than a lane holds")
             if r.prec not in precs:
                 raise ValueError(f"no lane serves precision {r.prec}")
         pending = {p: collections.deque() for p in precs}
         done: List[Request] = []
-        in_use = 0.0
+        in_use = self.ws_total   # the lanes' workspaces, then the requests in flight
         i = 0
         t0 = time.perf_counter()
         while len(done) < len(reqs):
@@ -235,6 +262,8 @@ class Server:
                     while q and len(batch) < self.max_batch:
                         b = request_bytes(q[0].n, q[0].prec)
                         if in_use + need + b > self.mem_cap:
+                            break
+                        if batch and self._ws_need([r.n for r in batch] + [q[0].n], ln.prec) > ln.ws_bytes:
                             break
                         r = q.popleft()
                         r.t_admit = time.perf_counter() - t0

@@ -29,11 +29,16 @@ def _stream(serving, count, n_hi, seed=5):
 def test_served_equals_alone(srv):
     reqs = _stream(srv, 48, 600)
     assert {r.prec for r in reqs} == {"fp64", "bf16x6"}
-    server = srv.Server(DEV, mem_cap=24e6, lanes_per_prec=2, max_batch=8, keep_results=True)
+    # a 24 MB budget for requests in flight on top of the four lanes' workspaces
+    ws = sum(2 * srv.lane_workspace_bytes(DEV, p, n_max=600) for p in ("fp64", "bf16x6"))
+    cap = ws + 24e6
+    server = srv.Server(DEV, mem_cap=cap, lanes_per_prec=2, max_batch=8, keep_results=True,
+                        precisions=("fp64", "bf16x6"), n_max=600)
     done = server.run(reqs)
     torch.cuda.synchronize()
     assert len(done) == len(reqs)
-    assert server.peak_bytes <= 24e6
+    assert server.ws_total <= ws * (1 + 1e-9) + 4096
+    assert server.peak_bytes <= cap
     batches = {r.t_admit for r in done}
     assert len(batches) > 2          # requests were admitted over several batches
     for r in done:
@@ -46,7 +51,7 @@ def test_served_equals_alone(srv):
 
 def test_served_matches_oracle(srv):
     reqs = [r for r in _stream(srv, 30, 300, seed=9) if r.prec == "fp64"][:6]
-    server = srv.Server(DEV, mem_cap=1e9, lanes_per_prec=2, max_batch=4, keep_results=True)
+    server = srv.Server(DEV, mem_cap=4e9, lanes_per_prec=2, max_batch=4, keep_results=True, n_max=300)
     done = server.run(reqs, realtime=False)
     torch.cuda.synchronize()
     for r in done:
@@ -61,8 +66,10 @@ def test_served_matches_oracle(srv):
 
 def test_admission_with_tight_budget(srv):
     reqs = _stream(srv, 12, 400, seed=11)
-    cap = max(srv.request_bytes(r.n, r.prec) for r in reqs) * 1.01
-    server = srv.Server(DEV, mem_cap=cap, lanes_per_prec=1, max_batch=16)
+    ws = sum(srv.lane_workspace_bytes(DEV, p, n_max=400) for p in ("fp64", "bf16x6"))
+    cap = ws + 4096 + max(srv.request_bytes(r.n, r.prec) for r in reqs) * 1.01
+    server = srv.Server(DEV, mem_cap=cap, lanes_per_prec=1, max_batch=16, precisions=("fp64", "bf16x6"),
+                        n_max=400)
     done = server.run(reqs, realtime=False)
     assert len(done) == len(reqs)
     assert server.peak_bytes <= cap

@@ -65,10 +65,16 @@ class _FakeServer(serving.Server):
         self.depth = int(depth)
         self.keep = False
         self.lanes = [_FakeLane(p) for p in precisions for _ in range(lanes_per_prec)]
+        for ln in self.lanes:
+            ln.ws_bytes = 3 * 8 * 1024 * 1024   # a fake workspace: room for three n = 1024 problems
+        self.ws_total = 0.0
         self.peak_bytes = 0.0
         self.log_lock = threading.Lock()
         self.launches = []           # (lane, [rid], bytes in flight incl. this batch, outstanding batches)
         self.flight = 0.0
+
+    def _ws_need(self, ns, prec):  # a fake workspace bound: 8 bytes an element of each problem
+        return sum(8 * n * n for n in ns)
 
     def _launch(self, lane, batch):
         b = sum(serving.request_bytes(r.n, r.prec) for r in batch)
@@ -116,6 +122,7 @@ def test_admission_respects_budget_depth_and_order(cap, lanes, max_batch, depth)
     for lane, rids, flight, outstanding in srv.launches:
         assert flight <= cap * (1 + 1e-12)
         assert 1 <= len(rids) <= max_batch
+        assert srv._ws_need([by_id[rid].n for rid in rids], lane.prec) <= lane.ws_bytes  # fits the workspace
         assert outstanding <= depth
         assert all(by_id[rid].prec == lane.prec for rid in rids)
     for prec in ("fp64", "bf16x6"):
