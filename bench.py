@@ -337,8 +337,8 @@ def fp64_peak_leg(dev):
         torch.cuda.synchronize()
         out[kind + "_tflops"] = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
     out["derived_dfma_tflops"] = FP64_PEAK_TFLOPS
-    out["how"] = ("4 CTAs x 256 threads per SM, register operands only: 8 independent FMA chains a thread "
-                  "(dfma) or 4 chains of mma.sync m8n8k4 f64 a thread (dmma); CUDA events")
+    out["how"] = ("4 CTAs x 256 threads per SM, register operands only: a 4 x 2 outer product of FMAs a "
+                  "thread (dfma) or 4 chains of mma.sync m8n8k4 f64 a thread (dmma); CUDA events")
     return out
 
 

@@ -290,9 +290,21 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
                         long long ldb, double *C, long long ldc, int prec, int lower, void *stream);
 
 /*
+ * Diagnostic (no counterpart in the paper): the FP64 reciprocal and square
+ * root that the diagonal factorisation uses on its pivots, applied to the n
+ * device values x[i] > 0: recip[i] ~ 1 / x[i] (an FP32 seed refined by one
+ * Householder step of order 2), sq[i] ~ sqrt(x[i]) and rsq[i] ~ 1 / sqrt(x[i])
+ * (Goldschmidt's iteration from an FP32 seed).  Zero, subnormal, infinite
+ * and NaN inputs take the platform's division and square root.  Device
+ * arrays of n doubles; asynchronous on stream.
+ */
+int cd_debug_fp64_helpers(cd_handle *h, int n, const double *x, double *recip, double *sq, double *rsq,
+                          void *stream);
+
+/*
  * Measurement support (no counterpart in the paper): the rate of the FP64
  * pipe.  Launches 4 CTAs of 256 threads per SM, each thread running `iters`
- * rounds of register-only FP64 work: kind 0 eight independent FMA chains
+ * rounds of register-only FP64 work: kind 0 a 4 x 2 outer product of FMAs
  * (DFMA, the instruction of the FP64 products here), kind 1 four chains of
  * the FP64 matrix instruction mma.sync m8n8k4 (DMMA).  *flops receives the
  * floating-point operations launched (2 per multiply-add); the caller times

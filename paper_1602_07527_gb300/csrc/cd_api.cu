@@ -2426,6 +2426,15 @@ int cd_chol_jacobian(cd_handle *h, int n, const double *L, long long ldl, double
   return c.err;
 }
 
+int cd_debug_fp64_helpers(cd_handle *h, int n, const double *x, double *recip, double *sq, double *rsq,
+                          void *stream) {
+  if (!h || n < 0 || (n > 0 && (!x || !recip || !sq || !rsq))) return CD_EINVAL;
+  DeviceGuard guard(h->device);
+  const cudaError_t e = launch_fp64_helpers(n, x, recip, sq, rsq, (cudaStream_t)stream);
+  ++h->launches;
+  return e == cudaSuccess ? CD_OK : CD_ECUDA;
+}
+
 int cd_debug_fp64_probe(cd_handle *h, int kind, long long iters, void *stream, double *flops) {
   if (!h || (kind != 0 && kind != 1) || iters < 1 || !flops) return CD_EINVAL;
   DeviceGuard guard(h->device);

@@ -462,13 +462,16 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
 // L as it is finished.  The tile is factorised right-looking in 16-column
 // panels (chol_blocked of Sec. 4.2 inside the tile):
 //   (a) the owners of the panel's diagonal-block rows send them to all CTAs;
-//   (b) every CTA factorises that block redundantly, pipelined over four
-//       warps (one per sub-partition): warp 0 forms each pivot's reciprocal
-//       square root by Goldschmidt's iteration (seven FP64 operations instead
-//       of a square root and a division), scales the column, publishes it and
-//       applies it to the next column at once (lookahead of one), while warps
-//       1-3 apply it to the later columns -- the pivot chain costs about nine
-//       FP64 operations per column, and all CTAs take the same pivot decisions;
+//   (b) every CTA factorises that block redundantly in its L D L^T form,
+//       pipelined over four warps (one per sub-partition): warp 0 forms each
+//       pivot's reciprocal (an FP32 seed and one Householder step: three FP64
+//       operations instead of a division), scales the column, publishes it
+//       and applies it to the next column at once (lookahead of one), while
+//       warps 1-3 apply it to the later columns -- the pivot chain costs five
+//       FP64 operations per column, and all CTAs take the same pivot
+//       decisions; the block's square roots and reciprocal square roots
+//       (Goldschmidt's iteration and two corrections) are then taken for all
+//       its columns at once, one thread each;
 //   (c) each CTA solves its own rows of the panel, C <- C D^{-T}, by forward
 //       substitution across the 16 lanes of a half-warp (each step: one
 //       multiply by the pivot's reciprocal, a shuffle, one multiply-add), and
@@ -542,8 +545,11 @@ __device__ __forceinline__ double scale_pow2(double v, int k) {
 // 1/sqrt(x) and sqrt(x) for a positive FP64 x by Goldschmidt's iteration
 // (g -> sqrt(m), h -> 1/(2 sqrt(m)); r = 1/2 - g h, g += g r, h += h r),
 // started from the FP32 hardware estimate of 1/sqrt(m), m = x 2^(-2k) in
-// [1, 4).  Two iterations take the 2^-23 start below FP64 rounding.
-// Subnormal and infinite x take the library square root.
+// [1, 4).  Two iterations take the 2^-23 start near FP64 rounding; a final
+// correction of the root from its residual m - g^2 and a Newton step of the
+// reciprocal root from the exact residual 1 - m y^2 bring both within one
+// unit in the last place (measured: the root correctly rounded).  Subnormal and infinite x
+// take the library square root.
 __device__ __forceinline__ void rsqrt_sqrt(double x, double &rs, double &sq) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)(b >> 52) & 0x7FF;
@@ -556,16 +562,24 @@ __device__ __forceinline__ void rsqrt_sqrt(double x, double &rs, double &sq) {
   const unsigned long long em = (unsigned long long)(e - 2 * k);  // 1023 or 1024
   const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | (em << 52)));
   const float mf = __uint_as_float((unsigned)((em - 896ull) << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
-  const double y = pos_f32_to_f64(rsqrtf(mf));
-  double g = m * y, h = scale_pow2(y, -1);
+  const double y0 = pos_f32_to_f64(rsqrtf(mf));
+  double g = m * y0, h = scale_pow2(y0, -1);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const double r = fma(-g, h, 0.5);
     g = fma(g, r, g);
     h = fma(h, r, h);
   }
+  // final corrections (Goldschmidt's iteration alone leaves up to about 1.5
+  // ulp): the root from its residual m - g^2 (exact through the FMA)
+  g = fma(h, fma(-g, g, m), g);
+  // y = 2 h ~ 1/sqrt(m): the residual 1 - m y^2 from the exact square
+  // y^2 = p + q (q by FMA), then y += (y / 2) residual
+  const double y = h + h;
+  const double p = y * y, q = fma(y, y, -p);
+  const double res = fma(-m, q, fma(-m, p, 1.0));
   sq = scale_pow2(g, k);
-  rs = scale_pow2(h, 1 - k);
+  rs = scale_pow2(fma(h, res, y), -k);
 }
 
 // 1/x for a positive normal FP64 x in three FP64 operations: the FP32
@@ -1047,6 +1061,25 @@ cudaError_t tile_kernels_init() {
   return cudaSuccess;
 }
 
+// The factorisation's FP64 reciprocal and square-root helpers applied to an
+// array, so that they can be checked against correctly rounded references.
+__global__ void k_fp64_helpers(int n, const double *x, double *recip, double *sq, double *rsq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  recip[i] = recip_pos(v);
+  double rs, s2;
+  rsqrt_sqrt(v, rs, s2);
+  sq[i] = s2;
+  rsq[i] = rs;
+}
+
+cudaError_t launch_fp64_helpers(int n, const double *x, double *recip, double *sq, double *rsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fp64_helpers<<<(n + 255) / 256, 256, 0, st>>>(n, x, recip, sq, rsq);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // FP64 peak probes (measurement support): the rate of the FP64 pipe as the
 // products above use it (DFMA) and of the FP64 matrix instruction
@@ -1055,18 +1088,34 @@ cudaError_t tile_kernels_init() {
 // values reached, but the compiler cannot know that.
 __device__ double g_fp64_sink;
 
+// DFMA: a 4 x 2 register outer product per thread, acc += a b^T, with a
+// rotated between rounds (register moves, off the FP64 pipe).  Measured on
+// GB300: small outer products (4 x 2, 2 x 2, 8 x 1) reach the same rate,
+// while shapes with more accumulators per operand (4 x 4, 3 x 4) lose about
+// a sixth to operand-register conflicts.
 __global__ void __launch_bounds__(256) k_dfma_probe(long long iters, double seed) {
-  double a[8];
+  double acc[4][2], a[4], b[2];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) a[c] = seed * (threadIdx.x + c + 1);
-  const double x = 1.0 - 1e-12, y = 1e-15;
-  for (long long i = 0; i < iters; ++i) {
+  for (int i = 0; i < 4; ++i) a[i] = seed * (threadIdx.x + i + 1);
+  b[0] = 1.0 - seed;
+  b[1] = 1.0 - 2.0 * seed;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], x, y);
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[i][0] = fma(a[i], b[0], acc[i][0]);
+      acc[i][1] = fma(a[i], b[1], acc[i][1]);
+    }
+    const double t = a[0];
+    a[0] = a[1];
+    a[1] = a[2];
+    a[2] = a[3];
+    a[3] = t;
   }
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) s += a[c];
+  for (int i = 0; i < 4; ++i) s += acc[i][0] + acc[i][1];
   if (s == 1234.5678) g_fp64_sink = s;
 }
 
@@ -1092,7 +1141,7 @@ cudaError_t launch_fp64_probe(int kind, int blocks, long long iters, cudaStream_
   const int threads = 256;
   if (kind == 0) {
     k_dfma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
-    *flops = 2.0 * 8.0 * (double)iters * threads * blocks;
+    *flops = 2.0 * 8.0 * (double)iters * threads * blocks;  // 4 x 2 multiply-adds a round
   } else {
     k_dmma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
     *flops = 2.0 * 256.0 * 4.0 * (double)iters * (threads / 32) * blocks;  // 8 x 8 x 4 per warp instruction

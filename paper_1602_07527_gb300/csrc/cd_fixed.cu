@@ -23,11 +23,13 @@
 //   over windows of 256 of K, so acc0-acc2 are exact in FP32 whatever
 //   the order and rounding of the tensor core's additions (every partial sum
 //   is an integer multiple of the last place below 2^24 units).  Each window
-//   ends with the three accumulators added, exactly, into a 64-bit integer
-//   FP64 (one rounding) and forms the output.  Thirteen slice products per
-//   multiply-add (s + t <= 4); error about 2^-32 |A_ik| max|B_j.| +
-//   2^-32 max|A_i.| |B_jk| per term from the operands' rounding, and below
-//   2^-40 max|A_i.| max|B_j.| from the products left out.
+//   ends with the four accumulators added (acc3 rounded to 2^-32) into a
+//   64-bit integer in units of 2^-32 held in the epilogue's registers; the
+//   last window converts it to FP64 (one rounding) and forms the output.
+//   Thirteen slice products per multiply-add (s + t <= 4); error about
+//   2^-32 |A_ik| max|B_j.| + 2^-32 max|A_i.| |B_jk| per term from the
+//   operands' rounding, and below 2^-40 max|A_i.| max|B_j.| from the
+//   products left out.
 //
 // One CTA per SM, persistent and warp-specialised as the split-BF16 product:
 //   warp 0   TMA loads of the four slices of A (128 x 64) and B (64 x 64) per

@@ -155,6 +155,8 @@ cudaError_t launch_subsym_group(const CopyGroup &g, cudaStream_t s);
 cudaError_t tile_kernels_init();
 // FP64 peak probes: kind 0 DFMA chains, 1 mma.sync m8n8k4 f64; *flops = work launched.
 cudaError_t launch_fp64_probe(int kind, int blocks, long long iters, cudaStream_t st, double *flops);
+// The diagonal factorisation's FP64 reciprocal and square-root helpers over an array.
+cudaError_t launch_fp64_helpers(int n, const double *x, double *recip, double *sq, double *rsq, cudaStream_t st);
 // Eq. delements: S (n^3 doubles) then J (n^4 doubles) from L and Linv = L^{-1}.
 cudaError_t launch_jacobian(int n, const double *L, long long ldl, const double *Li, long long ldi, double *S,
                             double *J, cudaStream_t s);

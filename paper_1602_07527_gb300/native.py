@@ -86,6 +86,7 @@ def lib():
         L.cd_chol_jacobian.argtypes = [_vp, _i, _vp, _ll, _vp, _vp]
         L.cd_get_last_device_error.argtypes = [_vp, P(_i)]
         L.cd_debug_fp64_probe.argtypes = [_vp, _i, _ll, _vp, P(ctypes.c_double)]
+        L.cd_debug_fp64_helpers.argtypes = [_vp, _i, _vp, _vp, _vp, _vp, _vp]
         L.cd_launch_count.argtypes = [_vp]
         L.cd_launch_count.restype = _ll
         L.cd_version.restype = ctypes.c_char_p
@@ -108,7 +109,7 @@ def exported_symbols():
             "cd_launch_count", "cd_version", "cd_profile_enable", "cd_profile_read", "cd_profile_timeline",
             "cd_chol_rev_noalloc", "cd_mixed_gemm_debug", "cd_set_priorities", "cd_debug_wait_timeout",
             "cd_chol_fwd_and_sens", "cd_chol_fwd_and_sens_batched", "cd_chol_jacobian", "cd_debug_fp64_probe",
-            "cd_workspace_size_batched", "cd_workspace_bytes"]
+            "cd_workspace_size_batched", "cd_workspace_bytes", "cd_debug_fp64_helpers"]
 
 
 def handle(device=None):
@@ -361,6 +362,17 @@ def fp64_probe(kind="dfma", iters=200000, device=None):
     _check(lib().cd_debug_fp64_probe(handle(dev), 0 if kind == "dfma" else 1, ctypes.c_longlong(iters), _stream(dev),
                                      ctypes.byref(fl)), "cd_debug_fp64_probe")
     return fl.value
+
+
+def fp64_helpers(x):
+    """The diagonal factorisation's FP64 helpers on a CUDA float64 vector x > 0:
+    returns (1/x, sqrt(x), 1/sqrt(x)) as computed on the device."""
+    if not x.is_cuda or x.dtype != torch.float64 or x.dim() != 1 or not x.is_contiguous():
+        raise TypeError("x must be a contiguous CUDA float64 vector")
+    r, s, q = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    _check(lib().cd_debug_fp64_helpers(handle(x.device), x.numel(), _vp(x.data_ptr()), _vp(r.data_ptr()),
+                                       _vp(s.data_ptr()), _vp(q.data_ptr()), _stream(x.device)), "cd_debug_fp64_helpers")
+    return r, s, q
 
 
 def launch_count(device=None, handle_=None):

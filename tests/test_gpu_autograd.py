@@ -1,6 +1,7 @@
 """Differentiation through the library: torch.autograd.Function whose backward
 is cd_chol_rev, on the Gaussian-process negative log marginal likelihood
-(inputs on [0,1]^4, targets iid N(0,1), theta = (s, l, sigma) = (1, 0.3, 0.1))."""
+(inputs on [0,1]^4, targets iid N(0,1), theta = (s, l, sigma) = (1, 0.3, 0.1)),
+at the GP configuration's sizes N = 2048 and 4096 and at a small N = 300."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,7 @@ def _grad(ag, X, y, theta, nb=0):
     return float(f.item()), th.grad.cpu().numpy()
 
 
-@pytest.mark.parametrize("n", [300, 2048])
+@pytest.mark.parametrize("n", [300, 2048, 4096])
 def test_gp_gradient_matches_oracle_and_fd(ag, n):
     Xn, yn = W.gp_case(n)
     X = torch.tensor(Xn, device=DEV)
