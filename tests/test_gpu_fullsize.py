@@ -1,10 +1,12 @@
 """Parity at the benchmark's sizes.
 
 N = 8192 (the timed configuration: SE covariance ell 0.3 on [0,1]^3 + 1e-4 I,
-default options): the oracle cannot run in seconds at this size, so each
-result is checked on sampled columns against the equation that defines it
-(Sigma = L L^T; Sigma_dot = L_dot L^T + L L_dot^T from Eq. symfwd;
-L^T (T + T^T) L = P + P^T from Eq. symrevtril), O(N^2) per column.
+default options): each result on sampled columns against the equation that
+defines it (Sigma = L L^T; Sigma_dot = L_dot L^T + L L_dot^T from Eq. symfwd;
+L^T (T + T^T) L = P + P^T from Eq. symrevtril), O(N^2) per column; and
+element by element against the full oracle (about a minute per routine on
+the host's cores), at the benchmark's jitter and at the jitter that keeps the
+condition number below 1e6.
 N = 2048 (same recipe): element by element against the full oracle.
 """
 import numpy as np

@@ -76,3 +76,24 @@ def test_admission_with_tight_budget(srv):
     s = srv.summarize(done)
     assert s["p99_ms"] >= s["p50_ms"] > 0
     server.close()
+
+
+def test_large_requests_served_equal_alone(srv):
+    # sizes up to the stream's maximum, where the split-BF16 passes take
+    # 256-wide blocks and the products split K: served bitwise equal to alone
+    sizes = [4096, 3000, 2100, 4096, 1500, 2600, 3500, 1100]
+    reqs = [srv.Request(rid=i, t_arrival=0.0, n=n, prec=("bf16x6" if i % 2 == 0 else "fp64"), seed=700 + i)
+            for i, n in enumerate(sizes)]
+    ws = sum(2 * srv.lane_workspace_bytes(DEV, p, n_max=4096) for p in ("fp64", "bf16x6"))
+    server = srv.Server(DEV, mem_cap=ws + 3e9, lanes_per_prec=2, max_batch=3, keep_results=True,
+                        precisions=("fp64", "bf16x6"), n_max=4096)
+    done = server.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    assert len(done) == len(reqs)
+    assert server.peak_bytes <= ws + 3e9
+    for r in done:
+        assert int(r.info.item()) == 0
+        _, alone, info = srv.solve_alone(r, DEV)
+        assert int(info.item()) == 0
+        assert torch.equal(r.sigma_bar, alone), (r.rid, r.n, r.prec)
+    server.close()
