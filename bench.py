@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--profile-pass", default=None, choices=["fwd", "sens", "rev", "fwd_and_sens"],
                     help="for profilers: run one pass of this operation on the --n workload and exit "
                          "(no timing, no JSON line); the factor it needs is computed first in FP64")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6"],
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6", "fixed4"],
                     help="precision of the --profile-pass operation")
     ap.add_argument("--timeline", action="store_true",
                     help="with --profile-pass: warm up, then print the recorded pass's launch timeline")

@@ -1090,7 +1090,8 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // ============================================================================
 constexpr int kMixMaxChunk = 2048;  // longest FP32 accumulation before an FP64 reduction
 constexpr int kMixMinKbPerSplit = 8;
-constexpr int kFixedSlices = 4;  // CD_MIXED_FIXED4: fixed-point slices per operand  // shortest K range (64-wide blocks) of one split-K part
+constexpr int kFixedSlices = 4;  // CD_MIXED_FIXED4: fixed-point slices per operand
+constexpr int kFixedMinKbPerSplit = 2;  // shortest K range (64-wide blocks) of one split-K part
 
 MOp mop(void *base, long long ld, long long rows, int T, int x0, int y0) {
   MOp o;
@@ -1236,7 +1237,9 @@ struct MixedBatch {
     if (t1 < 4LL * slots) {
       // each split keeps at least kMixMinKbPerSplit K blocks: a CTA's fixed
       // cost and the FP32 partial traffic outweigh finer parallelism
-      const int smax = std::min(64, std::max(1, kblocks / kMixMinKbPerSplit));
+      // (fixed-point products: their 64-bit partials are exact and cheap to
+      // sum, so a split may be as short as kFixedMinKbPerSplit blocks)
+      const int smax = std::min(64, std::max(1, kblocks / (fixed ? kFixedMinKbPerSplit : kMixMinKbPerSplit)));
       double best = wave_eff(t1, slots);
       for (int s2 = 2; s2 <= smax && best < 0.9; ++s2) {
         const double e = wave_eff(t1 * s2, slots);

@@ -23,7 +23,7 @@
 //   over windows of 256 of K, so acc0-acc2 are exact in FP32 whatever
 //   the order and rounding of the tensor core's additions (every partial sum
 //   is an integer multiple of the last place below 2^24 units).  Each window
-//   ends with the four accumulators added (acc3 rounded to 2^-32) into a
+//   ends with the four accumulators added (acc3 floored at 2^-32) into a
 //   64-bit integer in units of 2^-32 held in the epilogue's registers; the
 //   last window converts it to FP64 (one rounding) and forms the output.
 //   Thirteen slice products per multiply-add (s + t <= 4); error about
@@ -104,23 +104,21 @@ struct FGroup {
 };
 static_assert(sizeof(FGroup) <= 4096, "kernel parameter block too large");
 
-// round(f 2^32) as a 64-bit integer, from the bits of the binary32 f
-// (integer operations only).  Exact when f is a multiple of 2^-32, which
-// acc0, acc1 and acc2 are; acc3 is rounded to the nearest unit (ties away).
-// Zeros and subnormals give 0; the shift is clamped for values beyond any
-// reachable accumulator.
+// floor(f 2^32) as a 64-bit integer, from the bits of the binary32 f, in a
+// few integer operations: the signed significand placed in the high word and
+// shifted right arithmetically by 150 - exponent.  Exact when f is a
+// multiple of 2^-32, which acc0, acc1 and acc2 are; acc3 (below 2^-24 of
+// acc0's scale) is floored at 2^-32 of acc0's unit, 2^-46 of the product of
+// the row maxima.  Zeros give 0; every reachable accumulator has |f| < 2^23,
+// so the shift is at least 1.
 __device__ __forceinline__ long long f32_to_fix(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xFFu);
-  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = e - 118;  // f = m 2^(e - 150), so f 2^32 = m 2^(e - 118)
-  long long r;
-  if (sh >= 0)
-    r = m << min(sh, 39);
-  else
-    r = sh < -25 ? 0 : ((m >> (-sh - 1)) + 1) >> 1;
-  if (e == 0) r = 0;
-  return (b >> 31) ? -r : r;
+  const int b = __float_as_int(f);
+  const int e = (b >> 23) & 0xFF;
+  const int s = b >> 31;  // 0 or -1
+  const int m = (b & 0x7FFFFF) | (e ? 0x800000 : 0);
+  const int sm = (m ^ s) - s;
+  const int sh = max(1, min(150 - e, 63));
+  return ((long long)sm << 32) >> sh;
 }
 
 // v 2^e2 as the nearest binary64 (ties to even), integer operations only.
