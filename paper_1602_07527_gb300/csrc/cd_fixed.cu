@@ -410,14 +410,19 @@ __device__ __forceinline__ void epilogue(const FGroup &g, uint32_t tmem, double 
       tc_fence_after();
       const uint32_t acc = tmem + lane_base + (uint32_t)(b * kAccCols + 32 * half);
 #pragma unroll
-      for (int a = 0; a < kAccs; ++a) {
+      for (int a = 0; a < kAccs; ++a) {  // one accumulator's 32 columns: four loads, one wait
+        uint32_t x0[8], x1[8], x2[8], x3[8];
+        tmem_ld8(acc + (uint32_t)(a * FBN), x0);
+        tmem_ld8(acc + (uint32_t)(a * FBN + 8), x1);
+        tmem_ld8(acc + (uint32_t)(a * FBN + 16), x2);
+        tmem_ld8(acc + (uint32_t)(a * FBN + 24), x3);
+        tmem_wait_ld();
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          uint32_t x0[8];
-          tmem_ld8(acc + (uint32_t)(a * FBN + 8 * h), x0);
-          tmem_wait_ld();
-#pragma unroll
-          for (int q = 0; q < 8; ++q) tot[8 * h + q] += f32_to_fix(__uint_as_float(x0[q]));
+        for (int q = 0; q < 8; ++q) {
+          tot[q] += f32_to_fix(__uint_as_float(x0[q]));
+          tot[8 + q] += f32_to_fix(__uint_as_float(x1[q]));
+          tot[16 + q] += f32_to_fix(__uint_as_float(x2[q]));
+          tot[24 + q] += f32_to_fix(__uint_as_float(x3[q]));
         }
       }
       tc_fence_before();
