@@ -1093,30 +1093,33 @@ __device__ double g_fp64_sink;
 // GB300: small outer products (4 x 2, 2 x 2, 8 x 1) reach the same rate,
 // while shapes with more accumulators per operand (4 x 4, 3 x 4) lose about
 // a sixth to operand-register conflicts.
-__global__ void __launch_bounds__(256) k_dfma_probe(long long iters, double seed) {
-  double acc[4][2], a[4], b[2];
+template <int R, int C>
+__global__ void k_dfma_probe(long long iters, double seed) {
+  double acc[R][C], a[R], b[C];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) a[i] = seed * (threadIdx.x + i + 1);
-  b[0] = 1.0 - seed;
-  b[1] = 1.0 - 2.0 * seed;
+  for (int i = 0; i < R; ++i) a[i] = seed * (threadIdx.x + i + 1);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  for (int j = 0; j < C; ++j) b[j] = 1.0 - seed * (j + 1);
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < C; ++j) acc[i][j] = 0.0;
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      acc[i][0] = fma(a[i], b[0], acc[i][0]);
-      acc[i][1] = fma(a[i], b[1], acc[i][1]);
-    }
-    const double t = a[0];
-    a[0] = a[1];
-    a[1] = a[2];
-    a[2] = a[3];
-    a[3] = t;
-  }
-  double s = 0.0;
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-  for (int i = 0; i < 4; ++i) s += acc[i][0] + acc[i][1];
-  if (s == 1234.5678) g_fp64_sink = s;
+      for (int j = 0; j < C; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    const double t = a[0];
+#pragma unroll
+    for (int i = 0; i + 1 < R; ++i) a[i] = a[i + 1];
+    a[R - 1] = t;
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < C; ++j) sum += acc[i][j];
+  if (sum == 1234.5678) g_fp64_sink = sum;
 }
 
 __global__ void __launch_bounds__(256) k_dmma_probe(long long iters, double seed) {
@@ -1140,7 +1143,7 @@ __global__ void __launch_bounds__(256) k_dmma_probe(long long iters, double seed
 cudaError_t launch_fp64_probe(int kind, int blocks, long long iters, cudaStream_t st, double *flops) {
   const int threads = 256;
   if (kind == 0) {
-    k_dfma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
+    k_dfma_probe<4, 2><<<blocks, threads, 0, st>>>(iters, 1e-3);
     *flops = 2.0 * 8.0 * (double)iters * threads * blocks;  // 4 x 2 multiply-adds a round
   } else {
     k_dmma_probe<<<blocks, threads, 0, st>>>(iters, 1e-3);
