@@ -114,14 +114,31 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
-  for (int k0 = kfirst; k0 < khi; k0 += KB) {
+  // one K block of the staged operands into the accumulators
+  auto compute = [&](const double (*Ab)[TS + 1], const double (*Bb)[TS + 1]) {
+#pragma unroll
+    for (int kk = 0; kk < KB; ++kk) {
+      double a[RM], b[4];
+#pragma unroll
+      for (int r = 0; r < RM; ++r) a[r] = Ab[kk][ty + RT * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bb[kk][tx + CT * c];
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+  };
+  // this thread's share of the K block at k0, from global memory
+  double pa[LOADS], pb[LOADS];
+  auto gload = [&](int k0) {
 #pragma unroll
     for (int r = 0; r < LOADS; ++r) {
       const int e = tid + r * NT;
       int kk, ii;
       if (AM == A_T) { ii = e % TS; kk = e / TS; } else { kk = e % KB; ii = e / KB; }
       const int gi = m0 + ii, gk = k0 + kk;
-      As[kk][ii] = (gi < M && gk < khi) ? load_a<AM>(A, lda, gi, gk) : 0.0;
+      pa[r] = (gi < M && gk < khi) ? load_a<AM>(A, lda, gi, gk) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < LOADS; ++r) {
@@ -129,22 +146,47 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
       int kk, jj;
       if (BM == B_N) { jj = e % TS; kk = e / TS; } else { kk = e % KB; jj = e / KB; }
       const int gj = n0 + jj, gk = k0 + kk;
-      Bs[kk][jj] = (gj < N && gk < khi) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
+      pb[r] = (gj < N && gk < khi) ? load_b<BM>(B, ldb, gk, gj) : 0.0;
+    }
+  };
+  auto sstore = [&](double (*Ab)[TS + 1], double (*Bb)[TS + 1]) {
+#pragma unroll
+    for (int r = 0; r < LOADS; ++r) {
+      const int e = tid + r * NT;
+      if (AM == A_T) Ab[e / TS][e % TS] = pa[r]; else Ab[e % KB][e / KB] = pa[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LOADS; ++r) {
+      const int e = tid + r * NT;
+      if (BM == B_N) Bb[e / TS][e % TS] = pb[r]; else Bb[e % KB][e / KB] = pb[r];
+    }
+  };
+  if (TS == 64) {
+    // two staging buffers (As and Bs hold 2 KB rows each): the next block's
+    // global loads are in flight during this block's multiply-adds, and one
+    // barrier a block separates the buffers' reuse
+    int buf = 0;
+    if (kfirst < khi) {
+      gload(kfirst);
+      sstore(As, Bs);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < KB; ++kk) {
-      double a[RM], b[4];
-#pragma unroll
-      for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + RT * r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + CT * c];
-#pragma unroll
-      for (int r = 0; r < RM; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    for (int k0 = kfirst; k0 < khi; k0 += KB) {
+      const bool more = k0 + KB < khi;
+      if (more) gload(k0 + KB);
+      compute(As + buf * KB, Bs + buf * KB);
+      if (more) sstore(As + (buf ^ 1) * KB, Bs + (buf ^ 1) * KB);
+      __syncthreads();
+      buf ^= 1;
     }
-    __syncthreads();
+  } else {
+    for (int k0 = kfirst; k0 < khi; k0 += KB) {
+      gload(k0);
+      sstore(As, Bs);
+      __syncthreads();
+      compute(As, Bs);
+      __syncthreads();
+    }
   }
 
   const double alpha = d.alpha, beta = d.beta;
@@ -170,8 +212,9 @@ __device__ __forceinline__ void gemm_tile(const GemmGroup &g, int bid, double (*
 
 template <int AM, int BM, bool LOWER, int TS>
 __global__ void __launch_bounds__(gemm_threads<TS>(), TS == 32 ? 8 : 1) k_gemm_f64(const __grid_constant__ GemmGroup g) {
-  __shared__ double As[gemm_kblock<TS>()][TS + 1];
-  __shared__ double Bs[gemm_kblock<TS>()][TS + 1];
+  constexpr int kBufs = TS == 64 ? 2 : 1;  // 64 x 64 tiles stage the next K block during this one
+  __shared__ double As[kBufs * gemm_kblock<TS>()][TS + 1];
+  __shared__ double Bs[kBufs * gemm_kblock<TS>()][TS + 1];
   gemm_tile<AM, BM, LOWER, TS>(g, blockIdx.x, As, Bs);
 }
 
