@@ -90,9 +90,30 @@ def parse():
                          "(no timing, no JSON line); the factor it needs is computed first in FP64")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3", "bf16x6", "fixed4"],
                     help="precision of the --profile-pass operation")
+    ap.add_argument("--profile-gemm", default=None, metavar="M,N,K",
+                    help="for profilers: run the --prec tensor-core product (bf16x3, bf16x6 or fixed4) of "
+                         "random M x K and N x K operands three times and exit (no JSON line)")
     ap.add_argument("--timeline", action="store_true",
                     help="with --profile-pass: warm up, then print the recorded pass's launch timeline")
     return ap.parse_args()
+
+
+def profile_gemm(args):
+    """Three calls of one tensor-core product, for a profiler to capture the last."""
+    import torch
+    from paper_1602_07527_gb300 import native as nat
+    M, N, K = (int(v) for v in args.profile_gemm.split(","))
+    prec = args.prec if args.prec != "fp64" else "fixed4"
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    A = torch.randn(M, K, generator=g, device=dev, dtype=torch.float64)
+    B = torch.randn(N, K, generator=g, device=dev, dtype=torch.float64)
+    C = torch.zeros(M, N, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        nat.mixed_gemm_debug(A, B, C, prec=prec)
+    torch.cuda.synchronize()
+    print(f"profile product done: {prec} M={M} N={N} K={K}", file=sys.stderr)
+    return 0
 
 
 def profile_pass(args):
@@ -734,6 +755,8 @@ def serve_bench(args, dev):
 
 def main():
     args = parse()
+    if args.profile_gemm:
+        return profile_gemm(args)
     if args.profile_pass:
         return profile_pass(args)
     if args.impl == "reference":

@@ -2145,7 +2145,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   if (!bind_workspace(P, nb, ar)) return CD_ENOMEM;
   const bool mixed = opt.prec != CD_FP64;
   const bool fixed = opt.prec == CD_MIXED_FIXED4 && factor;
-  if (mixed && !mixed_available()) return CD_ECUDA;
+  if (mixed && mixed_init() != CD_OK) return CD_ECUDA;  // per device, once
   if (fixed && fixed_init() != CD_OK) return CD_ECUDA;
   if (mixed && !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar, fixed)) return CD_ENOMEM;
   // The step loops issue the diagonal chain on the high-priority stream (its
@@ -2475,7 +2475,7 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
   if (!A || !B || !C || lda < K || ldb < K || ldc < N) return CD_EINVAL;
   DeviceGuard guard(h->device);
   const bool fx = prec == CD_MIXED_FIXED4;
-  if (!mixed_available() || (fx && fixed_init() != CD_OK)) return CD_EINVAL;
+  if (mixed_init() != CD_OK || (fx && fixed_init() != CD_OK)) return CD_EINVAL;
   const int T = fx ? kFixedSlices : mix_terms(prec);
   const long long kp = (K + 63) / 64 * 64;
   const size_t bytes = kPartBytes + 2 * (size_t)T * ((size_t)M * kp + (size_t)N * kp) +
@@ -2518,7 +2518,7 @@ int cd_mixed_gemm_debug(cd_handle *h, int M, int N, int K, const double *A, long
 int cd_debug_wait_timeout(cd_handle *h, void *stream) {
   if (!h) return CD_EINVAL;
   DeviceGuard guard(h->device);
-  if (!mixed_available()) return CD_EINVAL;
+  if (mixed_init() != CD_OK) return CD_EINVAL;
   const int T = 2, K = 64, M = 64;
   const size_t bytes = 2 * (size_t)T * 2 * M * K + sizeof(double) * M * M + 4 * kAlign;
   cudaStream_t s = (cudaStream_t)stream;

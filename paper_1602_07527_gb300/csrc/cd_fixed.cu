@@ -622,12 +622,17 @@ int fsm_count() {
   return n;
 }
 
-bool g_fready = false;
+// Per device: function attributes (the dynamic shared-memory limit) are set
+// on the current device.
+constexpr int kMaxDev = 64;
+bool g_fready[kMaxDev];
 
 }  // namespace
 
 int fixed_init() {
-  if (g_fready) return CD_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return CD_ECUDA;
+  if (g_fready[dev]) return CD_OK;
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -650,7 +655,7 @@ int fixed_init() {
     cudaGetLastError();
     return CD_ECUDA;
   }
-  g_fready = true;
+  g_fready[dev] = true;
   return CD_OK;
 }
 

@@ -649,12 +649,22 @@ cudaError_t launch_one(const MGroup &g, cudaStream_t s, int max_units) {
   return cudaGetLastError();
 }
 
-bool g_ready = false;
+// Per device: function attributes (the dynamic shared-memory limit) are set
+// on the current device.
+constexpr int kMaxDev = 64;
+bool g_ready[kMaxDev];
+
+int current_device() {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDev ? dev : -1;
+}
 
 }  // namespace
 
 int mixed_init() {
-  if (g_ready) return CD_OK;
+  const int dev = current_device();
+  if (dev < 0) return CD_ECUDA;
+  if (g_ready[dev]) return CD_OK;
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -677,11 +687,14 @@ int mixed_init() {
     cudaGetLastError();
     return CD_ECUDA;
   }
-  g_ready = true;
+  g_ready[dev] = true;
   return CD_OK;
 }
 
-bool mixed_available() { return g_ready; }
+bool mixed_available() {
+  const int dev = current_device();
+  return dev >= 0 && g_ready[dev];
+}
 
 int mixed_ctas_per_sm() { return 1; }
 
