@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -324,6 +325,59 @@ struct GemmBatch {
     c.launch(name, flops, bytes, st, [&] { return launch_gemm_group(sub, st); });
     if (red) c.launch("splitk_reduce_f64", 0.0, rbytes, st, [&] { return launch_reduce_group(sub, st); });
   }
+  // Whether to split the last r row (or column) tiles of a problem f times further along
+  // K (a tail split): its CTAs carry equal work, one of them keeps its SM's
+  // FP64 unit busy, and the launch lasts as long as the most loaded SM.  With
+  // H whole units (tiles x splits) followed by T pieces of 1/f unit, handed
+  // out in order to the least loaded SM, the span is computed in closed form
+  // below; a tail split is taken when it is at least 3 % shorter.  The tail
+  // is the last row tiles (A and C offset by rows) or, for A views that have
+  // no row offset (the symmetric ones), the last column tiles (B and C offset
+  // by columns).  Dense operands, general outputs and 64 x 64 tiles only; the
+  // choice depends on the problem's shape alone.
+  bool tail_split(const GemmDesc &d, int ts, int sp, int kchunk, int &r_out, int &f_out, bool &cols_out) const {
+    if (ts != 64 || g.lower || g.tri) return false;
+    const bool rows_ok = g.amode == A_N || g.amode == A_T;  // row tail: A and C offset by rows
+    const bool cols_ok = g.bmode == B_N || g.bmode == B_T;  // column tail: B and C offset by columns
+    if (!rows_ok && !cols_ok) return false;
+    const long long S = std::max(1, c.h->num_sms);
+    auto span = [&](long long H, long long T, int f) {
+      const long long q = H / S, rem = H % S;
+      if (T == 0) return (double)(rem ? q + 1 : q);
+      if (rem == 0) return q + std::ceil((double)T / S) / f;
+      const long long fill = (S - rem) * f;  // pieces that bring every SM to q + 1
+      if (T <= fill) return (double)(q + 1);
+      return q + 1 + std::ceil((double)(T - fill) / S) / f;
+    };
+    const long long units = (long long)d.tiles_m * d.tiles_n * sp;
+    const double base = span(units, 0, 1);
+    double best = base;
+    int br = 0, bf = 1;
+    bool bcols = false;
+    for (int side = 0; side < 2; ++side) {
+      const bool cols = side == 1;
+      if (cols ? !cols_ok : !rows_ok) continue;
+      const long long per = (long long)(cols ? d.tiles_m : d.tiles_n) * sp;  // units of one row (column) of tiles
+      const int lines = cols ? d.tiles_n : d.tiles_m;
+      for (int f = 2; f <= 8; ++f) {
+        if (kchunk / f < 64) break;
+        for (int r = 1; r <= lines; ++r) {
+          const double v = span(units - r * per, r * per * f, f);
+          if (v < best - 1e-9) {
+            best = v;
+            br = r;
+            bf = f;
+            bcols = cols;
+          }
+        }
+      }
+    }
+    if (br == 0 || best > 0.97 * base) return false;
+    r_out = br;
+    f_out = bf;
+    cols_out = bcols;
+    return true;
+  }
   // One launch (or more, if the partial region fills) per tile size.
   void flush_ts(int ts) {
     GemmGroup sub;
@@ -339,24 +393,10 @@ struct GemmBatch {
     size_t used = 0;
     double flops = 0, bytes = 0, rbytes = 0;
     bool red = false;
-    for (int p = 0; p < g.count; ++p) {
-      GemmDesc d = g.d[p];
-      if (tile_size(d) != ts) continue;
-      d.tiles_m = (d.M + ts - 1) / ts;
-      d.tiles_n = (d.N + ts - 1) / ts;
-      int sp = std::min(choose_splits(d, ts), std::max(1, d.K / 16));
-      int kchunk = std::max(d.K, 1);
-      if (sp > 1) {
-        kchunk = ((d.K + sp - 1) / sp + 15) / 16 * 16;
-        sp = (d.K + kchunk - 1) / kchunk;
-      }
+    // one descriptor into the launch (partial region and descriptor slots permitting)
+    auto emit = [&](GemmDesc d, int sp, int kchunk) {
       const size_t mn = (size_t)d.M * d.N;
-      if (sp > 1 && (!part || mn * sp > part_cap)) {  // as many splits as the partial region holds
-        sp = part ? (int)std::max<size_t>(1, part_cap / mn) : 1;
-        kchunk = sp > 1 ? ((d.K + sp - 1) / sp + 15) / 16 * 16 : std::max(d.K, 1);
-        if (sp > 1) sp = (d.K + kchunk - 1) / kchunk;
-      }
-      if (sp > 1 && used + mn * sp > part_cap) {  // buffer full: launch what we have first
+      if ((sp > 1 && used + mn * sp > part_cap) || sub.count == kMaxGemm) {  // full: launch what we have first
         launch_sub(sub, red, flops, bytes, rbytes);
         sub.count = 0;
         sub.total_tiles = 0;
@@ -381,6 +421,59 @@ struct GemmBatch {
         red = true;
         rbytes += 8.0 * outs * (sp + (d.beta != 0.0 ? 2.0 : 1.0));
       }
+    };
+    for (int p = 0; p < g.count; ++p) {
+      GemmDesc d = g.d[p];
+      if (tile_size(d) != ts) continue;
+      d.tiles_m = (d.M + ts - 1) / ts;
+      d.tiles_n = (d.N + ts - 1) / ts;
+      int sp = std::min(choose_splits(d, ts), std::max(1, d.K / 16));
+      int kchunk = std::max(d.K, 1);
+      if (sp > 1) {
+        kchunk = ((d.K + sp - 1) / sp + 15) / 16 * 16;
+        sp = (d.K + kchunk - 1) / kchunk;
+      }
+      const size_t mn = (size_t)d.M * d.N;
+      if (sp > 1 && (!part || mn * sp > part_cap)) {  // as many splits as the partial region holds
+        sp = part ? (int)std::max<size_t>(1, part_cap / mn) : 1;
+        kchunk = sp > 1 ? ((d.K + sp - 1) / sp + 15) / 16 * 16 : std::max(d.K, 1);
+        if (sp > 1) sp = (d.K + kchunk - 1) / kchunk;
+      }
+      // the last row tiles split further along K, so that every SM ends with
+      // about the same work (see tail_split)
+      int r = 0, f = 1;
+      bool cols = false;
+      if (tail_split(d, ts, sp, kchunk, r, f, cols) && part) {
+        GemmDesc h = d, t = d;
+        int head = 0;  // rows (columns) of the head; 0: the whole problem takes the finer split
+        if (!cols) {
+          head = (d.tiles_m - r) * ts;
+          h.M = head;
+          h.tiles_m = d.tiles_m - r;
+          t.M = d.M - head;
+          t.tiles_m = r;
+          t.A = g.amode == A_N ? d.A + (long long)head * d.lda : d.A + head;
+          if (d.Cin) t.Cin = d.Cin + (long long)head * d.ldcin;
+          t.Cout = d.Cout + (long long)head * d.ldcout;
+        } else {
+          head = (d.tiles_n - r) * ts;
+          h.N = head;
+          h.tiles_n = d.tiles_n - r;
+          t.N = d.N - head;
+          t.tiles_n = r;
+          t.B = g.bmode == B_N ? d.B + head : d.B + (long long)head * d.ldb;
+          if (d.Cin) t.Cin = d.Cin + head;
+          t.Cout = d.Cout + head;
+        }
+        const int kt = ((d.K + sp * f - 1) / (sp * f) + 15) / 16 * 16;
+        const int st = (d.K + kt - 1) / kt;
+        if ((size_t)t.M * t.N * st <= part_cap) {
+          if (head > 0) emit(h, sp, kchunk);
+          emit(t, st, kt);
+          continue;
+        }
+      }
+      emit(d, sp, kchunk);
     }
     launch_sub(sub, red, flops, bytes, rbytes);
   }
