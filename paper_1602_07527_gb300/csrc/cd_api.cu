@@ -52,17 +52,17 @@ struct Arena {
   }
 };
 
-// Default block sizes (measured on GB300).  FP64 passes are DFMA-bound and
-// insensitive to nb; split-BF16 reverse and forward-sensitivity passes are
-// bound by their sequence of steps and run fastest with 256-wide blocks at
-// large n; the split-BF16 factorisation is bound by its one-CTA diagonal
-// factorisations and prefers 128.
+// Default block sizes (measured on GB300, N = 8192).  The reverse and
+// forward-sensitivity passes run fastest with 256-wide blocks at large n:
+// split-BF16 ones are bound by their sequence of steps, and the FP64 ones
+// gain a little (chol_rev 1.176 -> 1.185, chol_fwd_sens 1.152 -> 1.159
+// TFLOP/s).  The factorisations (and the one-loop pass) prefer 128: their
+// diagonal blocks factorise on one 8-CTA cluster (FP64 chol_fwd 1.154 at
+// 128, 1.088 at 256).
 int pick_nb(int n, const cd_options *opt, bool factorisation = false) {
   int nb = (opt && opt->nb > 0) ? opt->nb : (n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall);
-  if (opt && opt->prec != CD_FP64) {
-    if (opt->nb <= 0 && n >= 4096 && !factorisation) nb = 256;
-    nb = (nb + 63) / 64 * 64;  // the tensor-core path works on 64-wide K blocks
-  }
+  if (opt && opt->nb <= 0 && n >= 4096 && !factorisation) nb = 256;
+  if (opt && opt->prec != CD_FP64) nb = (nb + 63) / 64 * 64;  // the tensor-core path works on 64-wide K blocks
   return nb;
 }
 
