@@ -205,6 +205,14 @@ struct Ctx {
   void wait_mark() {
     if (side) cuda(cudaStreamWaitEvent(s, h->ev_mid, 0));
   }
+  // Named points in the side stream's work for the lookahead factorisation:
+  // record one after the side-stream work that s will need, wait on it later.
+  void record(cudaEvent_t e) {
+    if (side) cuda(cudaEventRecord(e, side));
+  }
+  void wait(cudaEvent_t e) {
+    if (side) cuda(cudaStreamWaitEvent(s, e, 0));
+  }
 };
 
 // Products of at most this many multiply-adds use 32 x 32 output tiles.
@@ -1614,27 +1622,42 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   auto Lop = [&](const Prob &p, int x0, int y0) {
     return fx ? fop(p.mx.fbig, (p.n + 63) / 64 * 64, p.n, p.mx.exL, x0, y0) : mop(p.mx.big, p.mx.ldb, p.n, T, x0, y0);
   };
-  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
-    c.fork();
-    {  // f1: D <- D - tril(R R^T), enqueued before the side stream's f3 so that its CTAs take SMs first
-      MixedBatch mb(c, T, true, false, "f1", fx);
+  // Lookahead.  Block column t is updated from the finished columns [0, j_t)
+  // in two parts: from [0, j_t - nb) on the side stream one step early,
+  // beside the diagonal tile of step t - 1 (f1 "old" and f3 "old"), and from
+  // the previous block column [j_t - nb, j_t) once it is split (f1 "new" on
+  // the chain, f3 "new" on the side stream).  The chain of a step is then
+  // the rank-nb update of the diagonal block, its factorisation, the panel
+  // solve and the split; the K = j_t products leave it.
+  auto upd = [&](int t, int k0, int k1, bool on_side, bool want_f1, bool want_f3) {
+    if (k1 <= k0) return;
+    if (want_f1) {
+      MixedBatch mb(c, T, true, on_side, "f1", fx);
       for (auto &p : P) {
-        const int j = s * nb;
+        const int j = t * nb;
         if (j >= p.n) continue;
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
-        mb.add(Lop(p, 0, j), Lop(p, 0, j), w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
+        mb.add(Lop(p, k0, j), Lop(p, k0, j), w, w, k1 - k0, D, p.ldx, D, p.ldx, -1.0, 1.0);
       }
     }
-    {  // f3 (side stream): C <- C - B R^T
-      MixedBatch mb(c, T, false, true, "f3", fx);
+    if (want_f3) {
+      MixedBatch mb(c, T, false, on_side, "f3", fx);
       for (auto &p : P) {
-        const int j = s * nb;
+        const int j = t * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
         double *C = p.X + (long long)k * p.ldx + j;
-        mb.add(Lop(p, 0, k), Lop(p, 0, j), m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
+        mb.add(Lop(p, k0, k), Lop(p, k0, j), m, w, k1 - k0, C, p.ldx, C, p.ldx, -1.0, 1.0);
       }
+    }
+  };
+  bool look_set[2] = {false, false};
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    const int j = s * nb;
+    if (s >= 1) {  // f1, new part: the previous block column, after the old part on the side stream
+      if (look_set[s & 1]) c.wait(c.h->ev_look[s & 1]);
+      upd(s, j - nb, j, false, true, false);
     }
     {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
       TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
@@ -1658,12 +1681,11 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
       tb.flush();
     }
-    c.join();
+    if (s >= 1) c.wait(c.h->ev_near);  // f3 (both parts) of this block column
     {  // f4: C <- C tril(D)^{-T}
       if (fx) {
         FSplitBatch sb(c, true);
         for (auto &p : P) {
-          const int j = s * nb;
           if (j >= p.n) continue;
           const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
           if (m <= 0) continue;
@@ -1673,7 +1695,6 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       } else {
         SplitBatch sb(c);
         for (auto &p : P) {
-          const int j = s * nb;
           if (j >= p.n) continue;
           const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
           if (m <= 0) continue;
@@ -1683,7 +1704,6 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
       MixedBatch mb(c, T, false, false, "f4", fx);
       for (auto &p : P) {
-        const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
         double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
@@ -1699,7 +1719,6 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       if (fx) {
         FSplitBatch sb(c, false);
         for (auto &p : P) {
-          const int j = s * nb;
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
           sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j, j,
@@ -1708,12 +1727,22 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       } else {
         SplitBatch sb(c);
         for (auto &p : P) {
-          const int j = s * nb;
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
           sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
                  w, j, j, T);
         }
+      }
+    }
+    if (s + 1 < steps) {  // side stream: the next block column's new f3 part, then block s + 2's old parts
+      c.fork();
+      upd(s + 1, j, j + nb, true, false, true);
+      c.record(c.h->ev_near);
+      if (s + 2 < steps) {
+        upd(s + 2, 0, j + nb, true, true, false);
+        c.record(c.h->ev_look[(s + 2) & 1]);
+        look_set[(s + 2) & 1] = true;
+        upd(s + 2, 0, j + nb, true, false, true);
       }
     }
   }
@@ -2377,7 +2406,10 @@ int cd_create(cd_handle **h, int device) {
       cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&x->ev_mid, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&x->ev_mid, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_look[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_look[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_near, cudaEventDisableTiming) != cudaSuccess) {
     cudaFree(x->dev_err);
     free(x);
     return CD_ECUDA;
@@ -2395,6 +2427,9 @@ int cd_destroy(cd_handle *h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->crit) cudaStreamDestroy(h->crit);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  for (int q = 0; q < 2; ++q)
+    if (h->ev_look[q]) cudaEventDestroy(h->ev_look[q]);
+  if (h->ev_near) cudaEventDestroy(h->ev_near);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);

@@ -134,6 +134,8 @@ struct cd_handle {
   cudaStream_t crit;           // high-priority stream for the diagonal (critical) chain
   cudaEvent_t ev_fork, ev_join, ev_in, ev_out;
   cudaEvent_t ev_mid;          // a point inside the side stream's work of a step
+  cudaEvent_t ev_look[2];      // lookahead factorisation: side-stream work issued one step early (by parity)
+  cudaEvent_t ev_near;         // lookahead factorisation: the current step's side-stream update
 };
 
 namespace cd {
