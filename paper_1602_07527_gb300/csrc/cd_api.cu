@@ -1231,7 +1231,8 @@ struct SplitBatch {
   Ctx &c;
   std::vector<SplitArgs> v;
   double bytes = 0;
-  explicit SplitBatch(Ctx &ctx) : c(ctx) {}
+  cudaStream_t st;
+  explicit SplitBatch(Ctx &ctx, bool on_side = false) : c(ctx), st(on_side && ctx.side ? ctx.side : ctx.s) {}
   void add(const double *src, long long lds, int rows, int cols, int mode, int transpose, void *dst, long long ldd,
            long long dst_rows, int reg_r0, int reg_c0, int h, int w, int dst_r0, int dst_c0, int T) {
     if (h <= 0 || w <= 0) return;
@@ -1246,9 +1247,9 @@ struct SplitBatch {
   }
   void flush() {
     if (v.empty()) return;
-    c.launch("split_bf16", 0.0, bytes, [&] {
+    c.launch("split_bf16", 0.0, bytes, st, [&] {
       int l = 0;
-      const cudaError_t e = mixed_split_group_launch(v.data(), (int)v.size(), c.s, &l);
+      const cudaError_t e = mixed_split_group_launch(v.data(), (int)v.size(), st, &l);
       if (l > 1) c.h->launches += l - 1;
       return e;
     });
@@ -1265,7 +1266,9 @@ struct FSplitBatch {
   bool compute;
   std::vector<SplitArgs> v;
   double bytes = 0;
-  FSplitBatch(Ctx &ctx, bool compute_exponents) : c(ctx), compute(compute_exponents) {}
+  cudaStream_t st;
+  FSplitBatch(Ctx &ctx, bool compute_exponents, bool on_side = false)
+      : c(ctx), compute(compute_exponents), st(on_side && ctx.side ? ctx.side : ctx.s) {}
   void add(const double *src, long long lds, int rows, int cols, int mode, void *dst, long long ldd,
            long long dst_rows, int reg_r0, int reg_c0, int h, int w, int dst_r0, int dst_c0, int *ex) {
     if (h <= 0 || w <= 0) return;
@@ -1280,9 +1283,9 @@ struct FSplitBatch {
   }
   void flush() {
     if (v.empty()) return;
-    c.launch("split_fixed4", 0.0, bytes, [&] {
+    c.launch("split_fixed4", 0.0, bytes, st, [&] {
       int l = 0;
-      const cudaError_t e = fixed_split_group_launch(v.data(), (int)v.size(), compute, c.s, &l);
+      const cudaError_t e = fixed_split_group_launch(v.data(), (int)v.size(), compute, st, &l);
       if (l > 1) c.h->launches += l - 1;
       return e;
     });
@@ -1652,6 +1655,29 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
   };
+  // f4's panel operand: the panel C of block column t (final once f3 is done), split for the
+  // product with D^{-1}; it does not wait for the diagonal factorisation
+  auto split_panel = [&](int t, bool on_side) {
+    if (fx) {
+      FSplitBatch sb(c, true, on_side);
+      for (auto &p : P) {
+        const int jj = t * nb;
+        if (jj >= p.n) continue;
+        const int k = std::min(p.n, jj + nb), w = k - jj, m = p.n - k;
+        if (m <= 0) continue;
+        sb.add(p.X + (long long)k * p.ldx + jj, p.ldx, m, w, 0, p.mx.fP1, nb, p.n, 0, 0, m, nb, 0, 0, p.mx.exP1);
+      }
+    } else {
+      SplitBatch sb(c, on_side);
+      for (auto &p : P) {
+        const int jj = t * nb;
+        if (jj >= p.n) continue;
+        const int k = std::min(p.n, jj + nb), w = k - jj, m = p.n - k;
+        if (m <= 0) continue;
+        sb.add(p.X + (long long)k * p.ldx + jj, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+      }
+    }
+  };
   bool look_set[2] = {false, false};
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     const int j = s * nb;
@@ -1683,22 +1709,21 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     if (s >= 1) c.wait(c.h->ev_near);  // f3 (both parts) of this block column
     {  // f4: C <- C tril(D)^{-T}
+      if (s == 0) split_panel(0, false);  // later panels are split on the side stream (below)
       if (fx) {
         FSplitBatch sb(c, true);
         for (auto &p : P) {
           if (j >= p.n) continue;
-          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, p.mx.fP1, nb, p.n, 0, 0, m, nb, 0, 0, p.mx.exP1);
+          const int w = std::min(p.n, j + nb) - j;
+          if (p.n - j - w <= 0) continue;
           sb.add(p.dinv, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
         }
       } else {
         SplitBatch sb(c);
         for (auto &p : P) {
           if (j >= p.n) continue;
-          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+          const int w = std::min(p.n, j + nb) - j;
+          if (p.n - j - w <= 0) continue;
           sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
@@ -1734,9 +1759,11 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         }
       }
     }
-    if (s + 1 < steps) {  // side stream: the next block column's new f3 part, then block s + 2's old parts
+    if (s + 1 < steps) {  // side stream: the next block column's new f3 part and its panel split, then
+                          // block s + 2's old parts
       c.fork();
       upd(s + 1, j, j + nb, true, false, true);
+      split_panel(s + 1, true);
       c.record(c.h->ev_near);
       if (s + 2 < steps) {
         upd(s + 2, 0, j + nb, true, true, false);
