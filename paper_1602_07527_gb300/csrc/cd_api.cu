@@ -1681,10 +1681,6 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   bool look_set[2] = {false, false};
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     const int j = s * nb;
-    if (s >= 1) {  // f1, new part: the previous block column, after the old part on the side stream
-      if (look_set[s & 1]) c.wait(c.h->ev_look[s & 1]);
-      upd(s, j - nb, j, false, true, false);
-    }
     {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
       TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
@@ -1707,9 +1703,11 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
       tb.flush();
     }
-    if (s >= 1) c.wait(c.h->ev_near);  // f3 (both parts) of this block column
-    {  // f4: C <- C tril(D)^{-T}
-      if (s == 0) split_panel(0, false);  // later panels are split on the side stream (below)
+    // f3 (both parts) of this block column and its panel split, and the previous step's panel
+    // solve on the side stream (it reads the split inverse, overwritten below)
+    if (s >= 1) c.wait(c.h->ev_near);
+    if (s == 0) split_panel(0, false);  // later panels are split on the side stream (below)
+    {  // D^{-1} for the panel solve
       if (fx) {
         FSplitBatch sb(c, true);
         for (auto &p : P) {
@@ -1727,40 +1725,66 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
-      MixedBatch mb(c, T, false, false, "f4", fx);
+    }
+    // f4: C <- C tril(D)^{-T}.  The next diagonal block needs only the panel's top nb rows: those
+    // are solved and split on the chain; the other rows on the side stream.
+    const bool more = s + 1 < steps;
+    auto f4 = [&](bool top, bool on_side) {
+      MixedBatch mb(c, T, false, on_side, "f4", fx);
       for (auto &p : P) {
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
+        const int r0 = top ? 0 : (more ? nb : 0), r1 = top && more ? std::min(m, nb) : m;
+        if (r1 <= r0) continue;
+        double *Cb = p.X + (long long)(k + r0) * p.ldx + j;  // in place: the product reads only the split copies
         if (fx)
-          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, 0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), m, w, w, nullptr, 0,
-                 Cb, p.ldx, 1.0, 0.0);
+          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, r0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), r1 - r0, w, w,
+                 nullptr, 0, Cb, p.ldx, 1.0, 0.0);
         else
-          mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
-                 0.0);
+          mb.add(mop(p.mx.P1, nb, p.n, T, 0, r0), mop(p.mx.P4, nb, nb, T, 0, 0), r1 - r0, w, w, nullptr, 0, Cb,
+                 p.ldx, 1.0, 0.0);
       }
-    }
-    {  // the finished block column of L joins the split operand
+    };
+    // the finished rows [j + row0, j + row1) of this block column join the split operand
+    auto split_col = [&](bool top, bool on_side) {
       if (fx) {
-        FSplitBatch sb(c, false);
+        FSplitBatch sb(c, false, on_side);
         for (auto &p : P) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
-          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j, j,
-                 p.n - j, w, j, j, p.mx.exL);
+          const int h0 = top ? 0 : (more ? std::min(p.n - j, w + nb) : 0);
+          const int h1 = top && more ? std::min(p.n - j, w + nb) : p.n - j;
+          if (h1 <= h0) continue;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j + h0,
+                 j, h1 - h0, w, j, j, p.mx.exL);
         }
       } else {
-        SplitBatch sb(c);
+        SplitBatch sb(c, on_side);
         for (auto &p : P) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
-          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j,
-                 w, j, j, T);
+          const int h0 = top ? 0 : (more ? std::min(p.n - j, w + nb) : 0);
+          const int h1 = top && more ? std::min(p.n - j, w + nb) : p.n - j;
+          if (h1 <= h0) continue;
+          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j + h0, j,
+                 h1 - h0, w, j, j, T);
         }
       }
+    };
+    if (more) {
+      c.fork();  // the side stream starts the panel's other rows as soon as D^{-1} is split
+      f4(false, true);
+      split_col(false, true);
     }
-    if (s + 1 < steps) {  // side stream: the next block column's new f3 part and its panel split, then
-                          // block s + 2's old parts
+    f4(true, false);
+    split_col(true, false);
+    if (s + 1 < steps) {
+      // f1 of the next block column, new part (this block column), on the chain before the side
+      // stream's work so that its CTAs take SMs first; after the old part on the side stream
+      if (look_set[(s + 1) & 1]) c.wait(c.h->ev_look[(s + 1) & 1]);
+      upd(s + 1, j, j + nb, false, true, false);
+      // side stream: the next block column's new f3 part and its panel split, then block s + 2's
+      // old parts
       c.fork();
       upd(s + 1, j, j + nb, true, false, true);
       split_panel(s + 1, true);

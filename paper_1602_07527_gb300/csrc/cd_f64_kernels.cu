@@ -506,19 +506,19 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
 // panels (chol_blocked of Sec. 4.2 inside the tile):
 //   (a) the owners of the panel's diagonal-block rows send them to all CTAs;
 //   (b) every CTA factorises that block redundantly in its L D L^T form,
-//       pipelined over four warps (one per sub-partition): warp 0 forms each
-//       pivot's reciprocal (an FP32 seed and one Householder step: three FP64
-//       operations instead of a division), scales the column, publishes it
-//       and applies it to the next column at once (lookahead of one), while
-//       warps 1-3 apply it to the later columns -- the pivot chain costs five
-//       FP64 operations per column, and all CTAs take the same pivot
-//       decisions; the block's square roots and reciprocal square roots
-//       (Goldschmidt's iteration and two corrections) are then taken for all
-//       its columns at once, one thread each;
-//   (c) each CTA solves its own rows of the panel, C <- C D^{-T}, by forward
-//       substitution across the 16 lanes of a half-warp (each step: one
-//       multiply by the pivot's reciprocal, a shuffle, one multiply-add), and
-//       sends them to every CTA's copy of L;
+//       A = U diag(d) U^T with U unit lower, pipelined over four warps: warp
+//       0 forms each pivot's reciprocal (an FP32 estimate and one cubic
+//       correction: three FP64 operations instead of a division), U's column
+//       u = a / d, publishes a and u and applies them to the next column at
+//       once (lookahead of one), while warps 1-3 apply them to the later
+//       columns -- the pivot chain costs five FP64 operations per column, and
+//       all CTAs take the same pivot decisions; the block's square roots and
+//       reciprocal square roots (Goldschmidt's iteration and two corrections)
+//       are then taken for all its columns at once, one thread each;
+//   (c) each CTA solves its own rows of the panel, C <- C L_D^{-T} with
+//       L_D = U diag(sqrt(d)): forward substitution with U across the 16
+//       lanes of a half-warp (each step a shuffle and one multiply-add), then
+//       one multiply by 1/sqrt(d); it sends them to every CTA's copy of L;
 //   (d) each CTA applies the rank-16 update to its own trailing rows.
 // Two cluster barriers per panel.  The inverse then needs one exchange: CTA b
 // inverts diagonal block b (a forward-substitution sweep per column, again
@@ -626,21 +626,22 @@ __device__ __forceinline__ void rsqrt_sqrt(double x, double &rs, double &sq) {
 }
 
 // 1/x for a positive normal FP64 x in three FP64 operations: the FP32
-// reciprocal of x's significand m (truncated to 24 bits) starts one step of
-// the cubic iteration y <- y + y (e + e^2), e = 1 - m y (Householder's method
-// of order two), which takes the ~2^-23 start error e to ~e^3, below FP64
-// rounding; the exponent is applied with integer operations.  Subnormal,
-// infinite and very large x (whose reciprocal would be subnormal) divide.
+// approximate reciprocal (rcp.approx, relative error ~2^-23) of x's
+// significand m, truncated to 24 bits, moved to x's exponent with integer
+// operations, starts one step of the cubic iteration y <- y + y (e + e^2),
+// e = 1 - x y (Householder's method of order two), which takes the ~2^-22
+// start error e to ~e^3, below FP64 rounding.  Subnormal, infinite and very
+// large x (whose reciprocal would be subnormal) divide.
 __device__ __forceinline__ double recip_pos(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)(b >> 52) & 0x7FF;
   if (e == 0 || e >= 2045) return 1.0 / x;
-  const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));  // [1, 2)
-  const float mf = __uint_as_float((127u << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
-  const double y0 = pos_f32_to_f64(__frcp_rn(mf));  // in (0.5, 1]
-  const double em = fma(-m, y0, 1.0);
-  const double y = fma(y0, fma(em, em, em), y0);
-  return scale_pow2(y, 1023 - e);
+  const float mf = __uint_as_float((127u << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));  // [1, 2)
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));  // in [0.5, 1]
+  const double y0 = scale_pow2(pos_f32_to_f64(rf), 1023 - e);
+  const double em = fma(-x, y0, 1.0);
+  return fma(y0, fma(em, em, em), y0);
 }
 
 // Inverse of the lower kPb x kPb block of Lf at (c0, c0) (w x w used, rest
@@ -667,6 +668,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   __shared__ volatile int s_tmo;
   __shared__ __align__(8) uint64_t pub_bar, done_bar;
   __shared__ double acol[2 * kPb], ucol[2 * kPb];
+  __shared__ double Ut[kPb * kDgLd];  // the panel's unit-lower factor a / d (below the diagonal)
   const TileDesc &d = g.d[blockIdx.y];
   const int t = d.t;
   // Both exits below are taken by every CTA of the cluster alike (same
@@ -712,8 +714,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
       }
       cluster.sync();
       if (tid < 128) {  // (b) chol_unblocked of the block in its L D L^T form, redundantly in
-        // every CTA, pipelined: warp 0 (lanes = rows) forms pivot d's
-        // reciprocal (three FP64 operations), the column a scaled by it,
+        // every CTA, A = U diag(d) U^T, pipelined: warp 0 (lanes = rows) forms
+        // pivot d's reciprocal (three FP64 operations), the column a scaled by it,
         // u = a / d, publishes a and u, and applies them to the next column
         // at once; warps 1-3 apply them to the columns after that,
         // A(r, k) -= a(r) u(k).  The pivot chain is five FP64 operations a
@@ -734,6 +736,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
             if (r > c && r < w) {
               acol[(g & 1) * kPb + r] = a;
               ucol[(g & 1) * kPb + r] = u;
+              Ut[r * kDgLd + c] = u;  // U = a / d below the diagonal, for (c)
             }
             if (r == 0 && !ok && s_bad < 0) s_bad = c0 + c;
             __syncwarp();
@@ -777,18 +780,18 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
       }
       __syncthreads();
       if (s_bad >= 0) break;  // the same in every CTA: all factorised the same block
-      {  // (c) own rows below the block: forward substitution across each half-warp
+      {  // (c) own rows below the block: y = C U^{-T} with the unit-lower factor U = a / d by
+        // forward substitution across each half-warp (one FMA a step), then L = y / sqrt(d)
         const int li = tid / kPb, c = tid % kPb, i = rank + kCl * li;
         const bool act = li < nown && i >= c0 + w;
-        double acc = act && c < w ? R[li * kTileMax + c0 + c] : 0.0, lic = 0.0;
+        double acc = act && c < w ? R[li * kTileMax + c0 + c] : 0.0;
         // a warp whose two rows are both above the panel or absent has nothing to solve
         if (__any_sync(0xffffffffu, act))
-          for (int s2 = 0; s2 < w; ++s2) {
-          const double v = (c == s2) ? acc * rd[c0 + s2] : 0.0;
-          const double ls = __shfl_sync(0xffffffffu, v, s2, 16);
-          if (c == s2) lic = ls;
-          if (c > s2 && c < w) acc = fma(-ls, Lf[pk(c0 + c, c0 + s2)], acc);
-        }
+          for (int s2 = 0; s2 + 1 < w; ++s2) {
+            const double ys = __shfl_sync(0xffffffffu, acc, s2, 16);
+            if (c > s2 && c < w) acc = fma(-ys, Ut[c * kDgLd + s2], acc);
+          }
+        const double lic = acc * rd[c0 + c];
         if (act && c < w) {
           R[li * kTileMax + c0 + c] = lic;
 #pragma unroll
