@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "cd_internal.h"
@@ -154,6 +155,8 @@ struct Ctx {
   cudaStream_t side = nullptr;  // second stream (null: everything on s)
   double *part2 = nullptr;      // split-K partials of work on the side stream
   size_t part2_cap = 0;
+  double *part3 = nullptr, *part4 = nullptr;  // one-loop mixed pass: the sensitivity steps' partials
+  size_t part3_cap = 0;
   void check(cudaError_t e) {  // after a kernel launch
     ++h->launches;
     cuda(e);
@@ -1612,7 +1615,11 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 
 // chol_blocked (Sec. 4.2), products in split BF16; the finished columns of L
 // are split into `big` block column by block column.
-void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+// after(s), if given, is called once block column s of L is final on both streams (the one-loop
+// pass hangs its sensitivity step there); dinv_slots keeps every block's D^{-1} (slot s of
+// p.dinv, the last block's too) instead of reusing slot 0.
+void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
+                   const std::function<void(int)> *after = nullptr, bool dinv_slots = false) {
   const int T = P.empty() ? 2 : P[0].mx.T;
   const bool fx = c.opt->prec == CD_MIXED_FIXED4;
   int nmax = 0;
@@ -1681,6 +1688,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   bool look_set[2] = {false, false};
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     const int j = s * nb;
+    const size_t slot = dinv_slots ? (size_t)s * nb * nb : 0;  // this block's D^{-1}
     {  // f2: D <- chol_unblocked(D), then D^{-1}   (FP64)
       TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
@@ -1689,7 +1697,8 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, j + w < p.n ? p.dinv : nullptr, nb, w, p.info, p.col0 + j));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, (j + w < p.n || dinv_slots) ? p.dinv + slot : nullptr, nb, w, p.info,
+                       p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -1697,7 +1706,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
           if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
           run_fwd(c, sub, kTileMax, ar);
-          trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          trtri_big(c, D, p.ldx, p.dinv + slot, nb, w, ar);
           ar.off = mark;
         }
       }
@@ -1714,7 +1723,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
           if (p.n - j - w <= 0) continue;
-          sb.add(p.dinv, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
+          sb.add(p.dinv + slot, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
         }
       } else {
         SplitBatch sb(c);
@@ -1722,7 +1731,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
           if (p.n - j - w <= 0) continue;
-          sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+          sb.add(p.dinv + slot, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
     }
@@ -1778,6 +1787,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     }
     f4(true, false);
     split_col(true, false);
+    if (after) (*after)(s);
     if (s + 1 < steps) {
       // f1 of the next block column, new part (this block column), on the chain before the side
       // stream's work so that its CTAs take SMs first; after the old part on the side stream
@@ -1799,6 +1809,132 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   }
 }
 
+// One block step of chol_blocked_fwd (Sec. 4.2), products in split BF16: p.L is the factor
+// (its split `big` holds at least columns [0, j + nb)), p.X the sensitivity L_dot, whose finished
+// columns go to `big2`; p.dinv's slot s holds the block's D^{-1}.
+void sens_mixed_step(Ctx &c, std::vector<Prob> &P, int nb, int s, int T, Arena &ar) {
+  c.fork();
+  {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T) = D_dot - tril(P + P^T), P = R_dot R^T:
+     // one product into T1, then the symmetric update (enqueued before the side stream's g3,
+     // so that its CTAs take SMs first)
+    {
+      MixedBatch mb(c, T, false, false, "g1");
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int w = std::min(p.n, j + nb) - j;
+        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, nullptr, 0,
+               p.T1, nb, 1.0, 0.0);
+      }
+    }
+    CopyBatch sym(c, true);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n || j == 0) continue;  // j = 0: no columns to the left, no product
+      const int w = std::min(p.n, j + nb) - j;
+      sym.add(p.T1, nb, p.X + (long long)j * p.ldx + j, p.ldx, w, w);
+    }
+  }
+  for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T
+    MixedBatch mb(c, T, false, true, "g3");
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      double *Cd = p.X + (long long)k * p.ldx + j;
+      void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
+      mb.add(mop(a, p.mx.ldb, p.n, T, 0, k), mop(b, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldx, Cd, p.ldx, -1.0,
+             1.0);
+    }
+  }
+  {  // g2 as the products of Eq. symfwd (problems that use them)
+    std::vector<DiagRev> v;
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
+      const int w = std::min(p.n, j + nb) - j;
+      v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                   p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
+    }
+    if (!v.empty()) sens_diag_symbolic(c, v);
+  }
+  {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
+    TileBatch tb(c, T_SENS);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n || diag_symbolic(c, p, nb)) continue;
+      const int w = std::min(p.n, j + nb) - j;
+      const double *D = p.L + (long long)j * p.ldl + j;
+      double *Dd = p.X + (long long)j * p.ldx + j;
+      if (w <= kTileMax) {
+        tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
+      } else {
+        tb.flush();
+        size_t mark = ar.off;
+        std::vector<Prob> sub(1);
+        sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
+        if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+        run_sens(c, sub, kTileMax, ar);
+        ar.off = mark;
+      }
+    }
+  }
+  c.join();
+  {  // g4a: C_dot <- C_dot - C D_dot^T
+    {
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+    }
+    MixedBatch mb(c, T, false, false, "g4a");
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      double *Cd = p.X + (long long)k * p.ldx + j;
+      mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, j, k), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, Cd, p.ldx, Cd, p.ldx,
+             -1.0, 1.0);
+    }
+  }
+  {  // g4b: C_dot <- C_dot D^{-T}
+    {
+      SplitBatch sb(c);
+      for (auto &p : P) {
+        const int j = s * nb;
+        if (j >= p.n) continue;
+        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+        if (m <= 0) continue;
+        sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
+        sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+      }
+    }
+    MixedBatch mb(c, T, false, false, "g4b");
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
+      mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
+             0.0);
+    }
+  }
+  {
+    SplitBatch sb(c);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
+            w, j, j, T);
+    }
+  }
+}
+
 // chol_blocked_fwd (Sec. 4.2), products in split BF16: L is split once into
 // `big`, the finished columns of L_dot into `big2`.
 void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
@@ -1812,366 +1948,83 @@ void run_sens_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
-  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
-    c.fork();
-    {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T) = D_dot - tril(P + P^T), P = R_dot R^T:
-       // one product into T1, then the symmetric update (enqueued before the side stream's g3,
-       // so that its CTAs take SMs first)
-      {
-        MixedBatch mb(c, T, false, false, "g1");
-        for (auto &p : P) {
-          const int j = s * nb;
-          if (j >= p.n) continue;
-          const int w = std::min(p.n, j + nb) - j;
-          mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), w, w, j, nullptr, 0,
-                 p.T1, nb, 1.0, 0.0);
-        }
-      }
-      CopyBatch sym(c, true);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n || j == 0) continue;  // j = 0: no columns to the left, no product
-        const int w = std::min(p.n, j + nb) - j;
-        sym.add(p.T1, nb, p.X + (long long)j * p.ldx + j, p.ldx, w, w);
-      }
-    }
-    for (int term = 0; term < 2; ++term) {  // g3 (side stream): C_dot <- C_dot - B_dot R^T - B R_dot^T
-      MixedBatch mb(c, T, false, true, "g3");
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cd = p.X + (long long)k * p.ldx + j;
-        void *a = term == 0 ? p.mx.big2 : p.mx.big, *b = term == 0 ? p.mx.big : p.mx.big2;
-        mb.add(mop(a, p.mx.ldb, p.n, T, 0, k), mop(b, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldx, Cd, p.ldx, -1.0,
-               1.0);
-      }
-    }
-    {  // g2 as the products of Eq. symfwd (problems that use them)
-      std::vector<DiagRev> v;
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
-                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
-      }
-      if (!v.empty()) sens_diag_symbolic(c, v);
-    }
-    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
-      TileBatch tb(c, T_SENS);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n || diag_symbolic(c, p, nb)) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        const double *D = p.L + (long long)j * p.ldl + j;
-        double *Dd = p.X + (long long)j * p.ldx + j;
-        if (w <= kTileMax) {
-          tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
-        } else {
-          tb.flush();
-          size_t mark = ar.off;
-          std::vector<Prob> sub(1);
-          sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
-          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
-          run_sens(c, sub, kTileMax, ar);
-          ar.off = mark;
-        }
-      }
-    }
-    c.join();
-    {  // g4a: C_dot <- C_dot - C D_dot^T
-      {
-        SplitBatch sb(c);
-        for (auto &p : P) {
-          const int j = s * nb;
-          if (j >= p.n) continue;
-          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          sb.add(p.X + (long long)j * p.ldx + j, p.ldx, w, w, 1, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
-        }
-      }
-      MixedBatch mb(c, T, false, false, "g4a");
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cd = p.X + (long long)k * p.ldx + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, j, k), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, Cd, p.ldx, Cd, p.ldx,
-               -1.0, 1.0);
-      }
-    }
-    {  // g4b: C_dot <- C_dot D^{-T}
-      {
-        SplitBatch sb(c);
-        for (auto &p : P) {
-          const int j = s * nb;
-          if (j >= p.n) continue;
-          const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-          sb.add(p.dinv + (size_t)s * nb * nb, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
-        }
-      }
-      MixedBatch mb(c, T, false, false, "g4b");
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
-               0.0);
-      }
-    }
-    {
-      SplitBatch sb(c);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
-              w, j, j, T);
-      }
-    }
-  }
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) sens_mixed_step(c, P, nb, s, T, ar);
 }
 
-// chol_blocked with chol_blocked_fwd in the same loop (as run_dual), products
-// in split BF16: the finished columns of L are split into `big`, those of
-// L_dot into `big2`; D^{-1} is split once per step for both panel solves.
+// chol_blocked and chol_blocked_fwd (Sec. 4.1 takes both in one loop), products in split BF16
+// or, for the factor, fixed-point slices.  The factorisation runs as in run_fwd_mixed, bound by
+// its diagonal chain; each sensitivity step runs one block column behind it on a second chain
+// and bulk stream (crit2, side2), started by events recorded once the factor's block column
+// is final on both of the factorisation's streams, so that it fills the SMs the chain leaves
+// idle.  The sensitivity steps take every block's D^{-1} from its slot of p.dinv, their own
+// scratch (P2/P3 for the panel and D^{-1} splits of the three-term split, T1/T2, partials) and,
+// under fixed4, their own three-term split of each finished block column of L (in `big`).
 void run_dual_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
-  const int T = P.empty() ? 2 : P[0].mx.T;
-  const bool fx = c.opt->prec == CD_MIXED_FIXED4;  // L's products on fixed-point slices
+  const bool fx = c.opt->prec == CD_MIXED_FIXED4;
+  const int T = P.empty() ? 2 : P[0].mx.T;  // the derivative products' split
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
-  auto blk = [&](const Prob &p, int s, int &j, int &k) {
-    j = s * nb;
-    k = std::min(p.n, j + nb);
-    return j < p.n;
-  };
-  if (fx)  // row exponents of L from the diagonal of Sigma, before it is overwritten
-    for (auto &p : P)
-      c.launch("diag_exponents", 0.0, 12.0 * p.n,
-               [&] { return fixed_diag_exponents(p.X, p.ldx, p.n, p.mx.exL, c.s); });
-  const auto fL = [&](const Prob &p, int x0, int y0) {
-    return fop(p.mx.fbig, (p.n + 63) / 64 * 64, p.n, p.mx.exL, x0, y0);
-  };
-  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
-    c.fork();
-    if (fx) {  // f1 on fixed-point slices
-      MixedBatch mb(c, T, true, false, "f1", true);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *D = p.X + (long long)j * p.ldx + j;
-        mb.add(fL(p, 0, j), fL(p, 0, j), w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // f1: D <- D - tril(R R^T);  g1, first term: D_dot <- D_dot - tril(R_dot R^T).
-       // f1 and g1 are enqueued before the side stream's f3 and g3, so that their CTAs take SMs first.
-      MixedBatch mb(c, T, true, false, "f1+g1");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *D = p.X + (long long)j * p.ldx + j, *Dd = p.Xd + (long long)j * p.ldxd + j;
-        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
-        if (!fx) mb.add(R, R, w, w, j, D, p.ldx, D, p.ldx, -1.0, 1.0);
-        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), R, w, w, j, Dd, p.ldxd, Dd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // g1, second term: D_dot <- D_dot - tril(R R_dot^T)
-      MixedBatch mb(c, T, true, false, "g1");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *Dd = p.Xd + (long long)j * p.ldxd + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, j), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), w, w, j, Dd, p.ldxd,
-               Dd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    if (fx) {  // f3 on fixed-point slices (side stream)
-      MixedBatch mb(c, T, false, true, "f3", true);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *C = p.X + (long long)k * p.ldx + j;
-        mb.add(fL(p, 0, k), fL(p, 0, j), m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // f3: C <- C - B R^T;  g3, first term: C_dot <- C_dot - B_dot R^T   (side stream)
-      MixedBatch mb(c, T, false, true, "f3+g3");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *C = p.X + (long long)k * p.ldx + j, *Cd = p.Xd + (long long)k * p.ldxd + j;
-        const MOp R = mop(p.mx.big, p.mx.ldb, p.n, T, 0, j);
-        if (!fx) mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), R, m, w, j, C, p.ldx, C, p.ldx, -1.0, 1.0);
-        mb.add(mop(p.mx.big2, p.mx.ldb, p.n, T, 0, k), R, m, w, j, Cd, p.ldxd, Cd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // g3, second term: C_dot <- C_dot - B R_dot^T   (side stream)
-      MixedBatch mb(c, T, false, true, "g3");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *Cd = p.Xd + (long long)k * p.ldxd + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, 0, k), mop(p.mx.big2, p.mx.ldb, p.n, T, 0, j), m, w, j, Cd, p.ldxd,
-               Cd, p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // f2: D <- chol_unblocked(D) and its inverse, FP64 (wide blocks: both diagonal steps by recursion)
-      TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j;
-        double *D = p.X + (long long)j * p.ldx + j;
-        if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, (k < p.n || diag_symbolic(c, p, nb)) ? p.dinv : nullptr, nb, w, p.info,
-                       p.col0 + j));
-        } else {
-          tb.flush();
-          size_t mark = ar.off;
-          std::vector<Prob> sub(1);
-          sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
-          sub[0].Xd = p.Xd + (long long)j * p.ldxd + j;
-          sub[0].ldxd = p.ldxd;
-          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
-          run_dual(c, sub, kTileMax, ar);
-          if (k < p.n) trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
-          ar.off = mark;
-        }
-      }
-      tb.flush();
-    }
-    {  // g2 as the products of Eq. symfwd (FP64)
-      std::vector<DiagRev> v;
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k) || k - j > kTileMax || !diag_symbolic(c, p, nb)) continue;
-        v.push_back({p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.dinv, p.T1,
-                     p.T2, k - j, nb});
-      }
-      if (!v.empty()) sens_diag_symbolic(c, v);
-    }
-    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)   (FP64)
-      TileBatch tb(c, T_SENS);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k) || k - j > kTileMax || diag_symbolic(c, p, nb)) continue;
-        tb.add(tdesc(p.X + (long long)j * p.ldx + j, p.ldx, p.Xd + (long long)j * p.ldxd + j, p.ldxd, nullptr, 0,
-                     k - j));
-      }
-    }
-    c.join();
-    {  // f4: C <- C D^{-T}   (C -> P1, D^{-1} -> P4, tril(D_dot) -> P3 for g4)
-      {
-        SplitBatch sb(c);
-        for (auto &p : P) {
-          int j, k;
-          if (!blk(p, s, j, k)) continue;
-          const int w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          if (!fx) sb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-          sb.add(p.dinv, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
-          sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, w, w, 1, 0, p.mx.P3, nb, nb, 0, 0, nb, nb, 0, 0, T);
-        }
-      }
-      if (fx) {
-        FSplitBatch fb(c, true);
-        for (auto &p : P) {
-          int j, k;
-          if (!blk(p, s, j, k)) continue;
-          const int w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          fb.add(p.X + (long long)k * p.ldx + j, p.ldx, m, w, 0, p.mx.fP1, nb, p.n, 0, 0, m, nb, 0, 0, p.mx.exP1);
-          fb.add(p.dinv, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
-        }
-      }
-      MixedBatch mb(c, T, false, false, "f4", fx);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *Cb = p.X + (long long)k * p.ldx + j;  // in place: the product reads only the split copies
-        if (fx)
-          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, 0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), m, w, w, nullptr, 0,
-                 Cb, p.ldx, 1.0, 0.0);
-        else
-          mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldx, 1.0,
-                 0.0);
-      }
-    }
-    {  // the finished block column of L joins the split operand
-      SplitBatch sb(c);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        sb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, 0, p.mx.big, p.mx.ldb, p.n, j, j, p.n - j, w, j,
-               j, T);
-      }
-      if (fx) {  // and its fixed-point slices for L's own products
-        FSplitBatch fb(c, false);
-        for (auto &p : P) {
-          int j, k;
-          if (!blk(p, s, j, k)) continue;
-          const int w = k - j;
-          fb.add(p.X + (long long)j * p.ldx + j, p.ldx, p.n - j, w, 1, p.mx.fbig, (p.n + 63) / 64 * 64, p.n, j, j,
-                 p.n - j, w, j, j, p.mx.exL);
-        }
-      }
-    }
-    {  // g4a: C_dot <- C_dot - C D_dot^T
-      MixedBatch mb(c, T, false, false, "g4a");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *Cd = p.Xd + (long long)k * p.ldxd + j;
-        mb.add(mop(p.mx.big, p.mx.ldb, p.n, T, j, k), mop(p.mx.P3, nb, nb, T, 0, 0), m, w, w, Cd, p.ldxd, Cd,
-               p.ldxd, -1.0, 1.0);
-      }
-    }
-    {  // g4b: C_dot <- C_dot D^{-T}
-      {
-        SplitBatch sb(c);
-        for (auto &p : P) {
-          int j, k;
-          if (!blk(p, s, j, k)) continue;
-          const int w = k - j, m = p.n - k;
-          if (m <= 0) continue;
-          sb.add(p.Xd + (long long)k * p.ldxd + j, p.ldxd, m, w, 0, 0, p.mx.P1, nb, p.n, 0, 0, m, nb, 0, 0, T);
-        }
-      }
-      MixedBatch mb(c, T, false, false, "g4b");
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        double *Cb = p.Xd + (long long)k * p.ldxd + j;  // in place: the product reads only the split copies
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.P4, nb, nb, T, 0, 0), m, w, w, nullptr, 0, Cb, p.ldxd, 1.0,
-               0.0);
-      }
-    }
-    {  // the finished block column of L_dot joins its split operand
-      SplitBatch sb(c);
-      for (auto &p : P) {
-        int j, k;
-        if (!blk(p, s, j, k)) continue;
-        const int w = k - j, m = p.n - k;
-        sb.add(p.Xd + (long long)j * p.ldxd + j, p.ldxd, p.n - j, w, 1, 0, p.mx.big2, p.mx.ldb, p.n, j, j, p.n - j,
-               w, j, j, T);
-      }
+  std::vector<Prob> S = P;  // the sensitivity pass's view: L = the factor being formed, X = L_dot
+  for (auto &q : S) {
+    q.L = q.X;
+    q.ldl = q.ldx;
+    q.X = q.Xd;
+    q.ldx = q.ldxd;
+    q.Xd = nullptr;
+    if (!fx) {  // the factorisation splits its panel and D^{-1} into P1 / P4
+      q.mx.P1 = q.mx.P2;
+      q.mx.P4 = q.mx.P3;
     }
   }
+  auto split_L = [&](Ctx &cc, int s) {  // fixed4: the three-term split of L's block column s
+    if (!fx) return;                     // (the three-term factorisation writes it itself)
+    SplitBatch sb(cc);
+    for (auto &q : S) {
+      const int j = s * nb;
+      if (j >= q.n) continue;
+      const int w = std::min(q.n, j + nb) - j;
+      sb.add(q.L + (long long)j * q.ldl + j, q.ldl, q.n - j, w, 1, 0, q.mx.big, q.mx.ldb, q.n, j, j, q.n - j, w, j,
+             j, T);
+    }
+  };
+  cd_handle *h = c.h;
+  if (nb > kTileMax || !h->crit2 || !h->side2 || !c.part3) {
+    // wide blocks recurse through the shared arena: the two passes one after the other
+    run_fwd_mixed(c, P, nb, ar, nullptr, true);
+    c.join();
+    for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+      split_L(c, s);
+      sens_mixed_step(c, S, nb, s, T, ar);
+    }
+    return;
+  }
+  Ctx sc = c;
+  sc.s = h->crit2;
+  sc.side = h->side2;
+  sc.part = c.part3;
+  sc.part_cap = c.part3_cap;
+  sc.part2 = c.part4;
+  sc.part2_cap = c.part3_cap;
+  c.cuda(cudaEventRecord(h->ev_start2, c.s));
+  c.cuda(cudaStreamWaitEvent(sc.s, h->ev_start2, 0));
+  const std::function<void(int)> after = [&](int s) {
+    // block column s of L is final: its top rows on the chain, the rest on the side stream
+    c.cuda(cudaEventRecord(h->ev_colA, c.s));
+    c.cuda(cudaStreamWaitEvent(sc.s, h->ev_colA, 0));
+    if (c.side) {
+      c.cuda(cudaEventRecord(h->ev_colB, c.side));
+      c.cuda(cudaStreamWaitEvent(sc.s, h->ev_colB, 0));
+    }
+    if (sc.err != CD_OK) return;
+    split_L(sc, s);
+    sens_mixed_step(sc, S, nb, s, T, ar);
+  };
+  run_fwd_mixed(c, P, nb, ar, &after, true);
+  sc.join();
+  c.cuda(cudaEventRecord(h->ev_start2, sc.s));
+  c.cuda(cudaStreamWaitEvent(c.s, h->ev_start2, 0));
+  if (c.err == CD_OK && sc.err != CD_OK) c.err = sc.err;
 }
 
 enum Op { OP_FWD, OP_REV, OP_SENS, OP_DUAL };
@@ -2191,7 +2044,8 @@ size_t part_bytes(int nmax, int nb, bool mixed) {
 size_t need_bytes(const int *n, int batch, int nb, bool mixed = false, bool dual = false) {
   int nmax = 0;
   for (int i = 0; i < batch; ++i) nmax = std::max(nmax, n[i]);
-  size_t b = 2 * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 2 * kAlign;
+  // (the one-loop mixed pass runs its sensitivity steps on two more streams, with partials of their own)
+  size_t b = (dual && mixed ? 4 : 2) * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 4 * kAlign;
   for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb, dual) + 2 * kAlign;
   return b;
 }
@@ -2273,6 +2127,11 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   c.side = h->side;
   c.part2 = (double *)ar.take(pb);
   c.part2_cap = pb / sizeof(double);
+  if (op == OP_DUAL && opt.prec != CD_FP64) {
+    c.part3 = (double *)ar.take(pb);
+    c.part4 = (double *)ar.take(pb);
+    c.part3_cap = pb / sizeof(double);
+  }
   // CD_UPPER: each operand's upper triangle, transposed, in a workspace copy
   // (ld n) on which the lower-triangle algorithms run; results go back below.
   struct Copy {
@@ -2453,6 +2312,11 @@ int cd_create(cd_handle **h, int device) {
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&x->side, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
       cudaStreamCreateWithPriority(&x->crit, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&x->side2, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&x->crit2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_colA, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_colB, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x->ev_start2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&x->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -2477,6 +2341,11 @@ int cd_destroy(cd_handle *h) {
   if (h->dev_err) cudaFree(h->dev_err);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->crit) cudaStreamDestroy(h->crit);
+  if (h->side2) cudaStreamDestroy(h->side2);
+  if (h->crit2) cudaStreamDestroy(h->crit2);
+  if (h->ev_colA) cudaEventDestroy(h->ev_colA);
+  if (h->ev_colB) cudaEventDestroy(h->ev_colB);
+  if (h->ev_start2) cudaEventDestroy(h->ev_start2);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   for (int q = 0; q < 2; ++q)
     if (h->ev_look[q]) cudaEventDestroy(h->ev_look[q]);
@@ -2632,16 +2501,21 @@ int cd_set_priorities(cd_handle *h, int chain_priority, int bulk_priority) {
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   auto clamp = [&](int p) { return std::min(lo, std::max(hi, p)); };
   if (cudaDeviceSynchronize() != cudaSuccess) return CD_ECUDA;
-  cudaStream_t crit = nullptr, side = nullptr;
-  if (cudaStreamCreateWithPriority(&crit, cudaStreamNonBlocking, clamp(chain_priority)) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, clamp(bulk_priority)) != cudaSuccess) {
-    if (crit) cudaStreamDestroy(crit);
-    return CD_ECUDA;
-  }
+  cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};  // crit, side, crit2, side2
+  for (int q = 0; q < 4; ++q)
+    if (cudaStreamCreateWithPriority(&st[q], cudaStreamNonBlocking, clamp(q % 2 ? bulk_priority : chain_priority)) !=
+        cudaSuccess) {
+      for (int r = 0; r < q; ++r) cudaStreamDestroy(st[r]);
+      return CD_ECUDA;
+    }
   cudaStreamDestroy(h->crit);
   cudaStreamDestroy(h->side);
-  h->crit = crit;
-  h->side = side;
+  cudaStreamDestroy(h->crit2);
+  cudaStreamDestroy(h->side2);
+  h->crit = st[0];
+  h->side = st[1];
+  h->crit2 = st[2];
+  h->side2 = st[3];
   return CD_OK;
 }
 

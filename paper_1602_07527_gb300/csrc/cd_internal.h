@@ -136,6 +136,10 @@ struct cd_handle {
   cudaEvent_t ev_mid;          // a point inside the side stream's work of a step
   cudaEvent_t ev_look[2];      // lookahead factorisation: side-stream work issued one step early (by parity)
   cudaEvent_t ev_near;         // lookahead factorisation: the current step's side-stream update
+  // One-loop mixed pass: the sensitivity steps run one block column behind the factorisation
+  // on a chain and a bulk stream of their own, after events of the factorisation's two streams.
+  cudaStream_t crit2, side2;
+  cudaEvent_t ev_colA, ev_colB, ev_start2;
 };
 
 namespace cd {
