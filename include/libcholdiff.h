@@ -316,7 +316,7 @@ int cd_debug_fp64_probe(cd_handle *h, int kind, long long iters, void *stream, d
  * Scheduling knob (no counterpart in the paper).  Every call runs its
  * diagonal chain on one internal stream and the step's independent bulk
  * product on another, both forked from and joined back into the caller's
- * stream; the mixed-precision one-loop pass runs its sensitivity steps on a
+ * stream; the one-loop pass runs its sensitivity steps on a
  * second such pair.  This sets their CUDA stream priorities (clamped to the
  * device's range; lower numbers are higher priority; defaults: greatest for
  * the chains, least for the bulk).  Handles serving latency-critical work can

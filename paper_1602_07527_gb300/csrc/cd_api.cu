@@ -155,7 +155,7 @@ struct Ctx {
   cudaStream_t side = nullptr;  // second stream (null: everything on s)
   double *part2 = nullptr;      // split-K partials of work on the side stream
   size_t part2_cap = 0;
-  double *part3 = nullptr, *part4 = nullptr;  // one-loop mixed pass: the sensitivity steps' partials
+  double *part3 = nullptr, *part4 = nullptr;  // one-loop pass: the sensitivity steps' partials
   size_t part3_cap = 0;
   void check(cudaError_t e) {  // after a kernel launch
     ++h->launches;
@@ -630,7 +630,8 @@ void sens_diag_symbolic(Ctx &c, const std::vector<DiagRev> &v) {
 }
 
 // Forward declarations (recursive diagonal steps).
-void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
+void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar, const std::function<void(int)> *after = nullptr,
+             bool dinv_slots = false);
 void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
 void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar);
@@ -756,7 +757,9 @@ bool bind_workspace(std::vector<Prob> &P, int nb, Arena &ar) {
 }
 
 // ------------------------------- chol_blocked (Sec. 4.2) -------------------
-void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+// after(s) and dinv_slots as in run_fwd_mixed (block column s of L is final on the chain).
+void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar, const std::function<void(int)> *after,
+             bool dinv_slots) {
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
@@ -783,6 +786,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         gb.add(w, w, j, R, p.ldx, R, p.ldx, R + j, p.ldx, R + j, p.ldx, -1.0, 1.0);
       }
     }
+    const size_t slot = dinv_slots ? (size_t)s * nb * nb : 0;  // this block's D^{-1}
     {  // f2: D <- chol_unblocked(D); then the inverse of D for f4
       TileBatch tb(c, T_POTRF);  // factorisation and inverse of the diagonal block in one cluster launch
       for (auto &p : P) {
@@ -791,7 +795,8 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int k = std::min(p.n, j + nb), w = k - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, k < p.n ? p.dinv : nullptr, nb, w, p.info, p.col0 + j));
+          tb.add(tdesc(nullptr, 0, D, p.ldx, (k < p.n || dinv_slots) ? p.dinv + slot : nullptr, nb, w, p.info,
+                       p.col0 + j));
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -799,7 +804,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sub[0] = Prob{w, nullptr, 0, D, p.ldx, p.info, nullptr, nullptr, p.col0 + j};
           if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
           run_fwd(c, sub, kTileMax, ar);
-          trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
+          trtri_big(c, D, p.ldx, p.dinv + slot, nb, w, ar);
           ar.off = mark;
         }
       }
@@ -813,7 +818,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         const int j = s * nb;
         if (j >= p.n) continue;
         const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv, nb, nullptr, 0, p.W, nb, 1.0, 0.0);
+        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv + slot, nb, nullptr, 0, p.W, nb, 1.0, 0.0);
       }
     }
     {
@@ -825,6 +830,7 @@ void run_fwd(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
       }
     }
+    if (after) (*after)(s);
   }
 }
 
@@ -928,109 +934,113 @@ void run_rev(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 }
 
 // ------------------------------ chol_blocked_fwd (Sec. 4.2) ----------------
+// One block step of chol_blocked_fwd (Sec. 4.2) in FP64: p.L the factor (block columns [0, j + nb)
+// final), p.X the sensitivity L_dot, p.dinv's slot s the block's D^{-1}, p.W the panel scratch.
+void sens_step(Ctx &c, std::vector<Prob> &P, int nb, int s, Arena &ar) {
+  c.fork();  // g3 does not depend on g1 / g2 of this step
+  for (int term = 0; term < 2; ++term) {  // g3: C_dot <- C_dot - B_dot R^T - B R_dot^T
+    GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      double *Cd = p.X + (long long)k * p.ldx + j;
+      if (term == 0)
+        gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Cd, p.ldx, Cd,
+               p.ldx, -1.0, 1.0);
+      else
+        gb.add(m, w, j, p.L + (long long)k * p.ldl, p.ldl, p.X + (long long)j * p.ldx, p.ldx, Cd, p.ldx, Cd,
+               p.ldx, -1.0, 1.0);
+    }
+  }
+  for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
+    GemmBatch gb(c, A_N, B_T, true);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int w = std::min(p.n, j + nb) - j;
+      const double *Rd = p.X + (long long)j * p.ldx;
+      const double *R = p.L + (long long)j * p.ldl;
+      double *Dd = p.X + (long long)j * p.ldx + j;
+      if (term == 0)
+        gb.add(w, w, j, Rd, p.ldx, R, p.ldl, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
+      else
+        gb.add(w, w, j, R, p.ldl, Rd, p.ldx, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
+    }
+  }
+  {  // g2 as the products of Eq. symfwd (problems that use them)
+    std::vector<DiagRev> v;
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
+      const int w = std::min(p.n, j + nb) - j;
+      v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
+                   p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
+    }
+    if (!v.empty()) sens_diag_symbolic(c, v);
+  }
+  {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
+    TileBatch tb(c, T_SENS);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n || diag_symbolic(c, p, nb)) continue;
+      const int w = std::min(p.n, j + nb) - j;
+      const double *D = p.L + (long long)j * p.ldl + j;
+      double *Dd = p.X + (long long)j * p.ldx + j;
+      if (w <= kTileMax) {
+        tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
+      } else {
+        tb.flush();
+        size_t mark = ar.off;
+        std::vector<Prob> sub(1);
+        sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
+        if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
+        run_sens(c, sub, kTileMax, ar);
+        ar.off = mark;
+      }
+    }
+  }
+  c.join();
+  {  // g4a: C_dot <- C_dot - C D_dot^T
+    GemmBatch gb(c, A_N, B_TL, false);
+    gb.g.tri = TRI_B_UPPER;
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      double *Cd = p.X + (long long)k * p.ldx + j;
+      gb.add(m, w, w, p.L + (long long)k * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx, Cd, p.ldx, Cd,
+             p.ldx, -1.0, 1.0);
+    }
+  }
+  {  // g4b: C_dot <- C_dot D^{-T}   (into W, then copy back)
+    GemmBatch gb(c, A_N, B_T, false);
+    gb.g.tri = TRI_B_UPPER;
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv + (size_t)s * nb * nb, nb, nullptr, 0, p.W,
+             nb, 1.0, 0.0);
+    }
+  }
+  {
+    CopyBatch cb(c);
+    for (auto &p : P) {
+      const int j = s * nb;
+      if (j >= p.n) continue;
+      const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
+      cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
+    }
+  }
+}
+
 void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   precompute_dinv(c, P, nb, false, ar);
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
-  for (int s = 0; s < steps && c.err == CD_OK; ++s) {
-    c.fork();  // g3 does not depend on g1 / g2 of this step
-    for (int term = 0; term < 2; ++term) {  // g3: C_dot <- C_dot - B_dot R^T - B R_dot^T
-      GemmBatch gb(c, A_N, B_T, false, /*on_side=*/true);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cd = p.X + (long long)k * p.ldx + j;
-        if (term == 0)
-          gb.add(m, w, j, p.X + (long long)k * p.ldx, p.ldx, p.L + (long long)j * p.ldl, p.ldl, Cd, p.ldx, Cd,
-                 p.ldx, -1.0, 1.0);
-        else
-          gb.add(m, w, j, p.L + (long long)k * p.ldl, p.ldl, p.X + (long long)j * p.ldx, p.ldx, Cd, p.ldx, Cd,
-                 p.ldx, -1.0, 1.0);
-      }
-    }
-    for (int term = 0; term < 2; ++term) {  // g1: D_dot <- D_dot - tril(R_dot R^T + R R_dot^T)
-      GemmBatch gb(c, A_N, B_T, true);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        const double *Rd = p.X + (long long)j * p.ldx;
-        const double *R = p.L + (long long)j * p.ldl;
-        double *Dd = p.X + (long long)j * p.ldx + j;
-        if (term == 0)
-          gb.add(w, w, j, Rd, p.ldx, R, p.ldl, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
-        else
-          gb.add(w, w, j, R, p.ldl, Rd, p.ldx, Dd, p.ldx, Dd, p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // g2 as the products of Eq. symfwd (problems that use them)
-      std::vector<DiagRev> v;
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n || !diag_symbolic(c, p, nb)) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        v.push_back({p.L + (long long)j * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx,
-                     p.dinv + (size_t)s * nb * nb, p.T1, p.T2, w, nb});
-      }
-      if (!v.empty()) sens_diag_symbolic(c, v);
-    }
-    {  // g2: D_dot <- chol_unblocked_fwd(D, D_dot)
-      TileBatch tb(c, T_SENS);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n || diag_symbolic(c, p, nb)) continue;
-        const int w = std::min(p.n, j + nb) - j;
-        const double *D = p.L + (long long)j * p.ldl + j;
-        double *Dd = p.X + (long long)j * p.ldx + j;
-        if (w <= kTileMax) {
-          tb.add(tdesc(D, p.ldl, Dd, p.ldx, nullptr, 0, w));
-        } else {
-          tb.flush();
-          size_t mark = ar.off;
-          std::vector<Prob> sub(1);
-          sub[0] = Prob{w, D, p.ldl, Dd, p.ldx, nullptr, nullptr, nullptr, 0};
-          if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
-          run_sens(c, sub, kTileMax, ar);
-          ar.off = mark;
-        }
-      }
-    }
-    c.join();
-    {  // g4a: C_dot <- C_dot - C D_dot^T
-      GemmBatch gb(c, A_N, B_TL, false);
-      gb.g.tri = TRI_B_UPPER;
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        double *Cd = p.X + (long long)k * p.ldx + j;
-        gb.add(m, w, w, p.L + (long long)k * p.ldl + j, p.ldl, p.X + (long long)j * p.ldx + j, p.ldx, Cd, p.ldx, Cd,
-               p.ldx, -1.0, 1.0);
-      }
-    }
-    {  // g4b: C_dot <- C_dot D^{-T}   (into W, then copy back)
-      GemmBatch gb(c, A_N, B_T, false);
-      gb.g.tri = TRI_B_UPPER;
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        gb.add(m, w, w, p.X + (long long)k * p.ldx + j, p.ldx, p.dinv + (size_t)s * nb * nb, nb, nullptr, 0, p.W,
-               nb, 1.0, 0.0);
-      }
-    }
-    {
-      CopyBatch cb(c);
-      for (auto &p : P) {
-        const int j = s * nb;
-        if (j >= p.n) continue;
-        const int k = std::min(p.n, j + nb), w = k - j, m = p.n - k;
-        cb.add(p.W, nb, p.X + (long long)k * p.ldx + j, p.ldx, m, w);
-      }
-    }
-  }
+  for (int s = 0; s < steps && c.err == CD_OK; ++s) sens_step(c, P, nb, s, ar);
 }
 
 // ------------- chol_blocked with chol_blocked_fwd in the same loop ----------
@@ -1040,8 +1050,9 @@ void run_sens(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
 // columns and run on the side stream; the chain f1, g1, f2, g2 runs on the
 // high-priority stream; f4 and g4 then solve both panels with the one
 // inverse of the new diagonal block.  A diagonal block wider than one tile
-// is itself processed by this routine with tile-sized blocks.
-void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+// is itself processed by this routine with tile-sized blocks.  (Used for
+// blocks wider than one tile; run_dual pipelines the two passes otherwise.)
+void run_dual_loop(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   int nmax = 0;
   for (auto &p : P) nmax = std::max(nmax, p.n);
   const int steps = nblocks(nmax, nb);
@@ -1117,7 +1128,7 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
           sub[0].Xd = p.Xd + (long long)j * p.ldxd + j;
           sub[0].ldxd = p.ldxd;
           if (!bind_workspace(sub, kTileMax, ar)) { c.err = CD_ENOMEM; return; }
-          run_dual(c, sub, kTileMax, ar);
+          run_dual_loop(c, sub, kTileMax, ar);
           if (k < p.n) trtri_big(c, D, p.ldx, p.dinv, nb, w, ar);
           ar.off = mark;
         }
@@ -1185,6 +1196,46 @@ void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
   }
+}
+
+// chol_blocked and chol_blocked_fwd (Sec. 4.1 takes both in one loop) in FP64: the factorisation
+// as in run_fwd, each sensitivity step one block column behind it on a second chain and bulk
+// stream, started by an event once the block column of L is final, with every block's D^{-1}
+// in its slot of p.dinv and the sensitivity panel in W2.
+void run_dual(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
+  cd_handle *h = c.h;
+  if (nb > kTileMax || !h->crit2 || !h->side2 || !c.part3) {
+    run_dual_loop(c, P, nb, ar);
+    return;
+  }
+  std::vector<Prob> S = P;  // the sensitivity pass's view: L = the factor being formed, X = L_dot
+  for (auto &q : S) {
+    q.L = q.X;
+    q.ldl = q.ldx;
+    q.X = q.Xd;
+    q.ldx = q.ldxd;
+    q.W = q.W2;
+    q.Xd = nullptr;
+  }
+  Ctx sc = c;
+  sc.s = h->crit2;
+  sc.side = h->side2;
+  sc.part = c.part3;
+  sc.part_cap = c.part3_cap;
+  sc.part2 = c.part4;
+  sc.part2_cap = c.part3_cap;
+  c.cuda(cudaEventRecord(h->ev_start2, c.s));
+  c.cuda(cudaStreamWaitEvent(sc.s, h->ev_start2, 0));
+  const std::function<void(int)> after = [&](int s) {
+    c.cuda(cudaEventRecord(h->ev_colA, c.s));
+    c.cuda(cudaStreamWaitEvent(sc.s, h->ev_colA, 0));
+    if (sc.err == CD_OK) sens_step(sc, S, nb, s, ar);
+  };
+  run_fwd(c, P, nb, ar, &after, true);
+  sc.join();
+  c.cuda(cudaEventRecord(h->ev_start2, sc.s));
+  c.cuda(cudaStreamWaitEvent(c.s, h->ev_start2, 0));
+  if (c.err == CD_OK && sc.err != CD_OK) c.err = sc.err;
 }
 
 // ============================================================================
@@ -2044,8 +2095,8 @@ size_t part_bytes(int nmax, int nb, bool mixed) {
 size_t need_bytes(const int *n, int batch, int nb, bool mixed = false, bool dual = false) {
   int nmax = 0;
   for (int i = 0; i < batch; ++i) nmax = std::max(nmax, n[i]);
-  // (the one-loop mixed pass runs its sensitivity steps on two more streams, with partials of their own)
-  size_t b = (dual && mixed ? 4 : 2) * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 4 * kAlign;
+  // (the one-loop pass runs its sensitivity steps on two more streams, with partials of their own)
+  size_t b = (dual ? 4 : 2) * part_bytes(nmax, nb, mixed) + recursion_bytes(nb) + 4 * kAlign;
   for (int i = 0; i < batch; ++i) b += prob_bytes(n[i], nb, dual) + 2 * kAlign;
   return b;
 }
@@ -2127,7 +2178,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   c.side = h->side;
   c.part2 = (double *)ar.take(pb);
   c.part2_cap = pb / sizeof(double);
-  if (op == OP_DUAL && opt.prec != CD_FP64) {
+  if (op == OP_DUAL) {
     c.part3 = (double *)ar.take(pb);
     c.part4 = (double *)ar.take(pb);
     c.part3_cap = pb / sizeof(double);
