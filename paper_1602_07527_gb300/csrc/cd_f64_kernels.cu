@@ -525,17 +525,26 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
 // across half-warps) and sends it to all; each CTA then forms its own columns
 // of X = L^{-1} block row by block row, X_bi = D_bi^{-1} (E - L_{bi,<bi} X_{<bi}).
 // ---------------------------------------------------------------------------
-constexpr int kCl = 8;                     // CTAs per tile (portable cluster size)
+constexpr int kCl = 16;                    // CTAs per tile (a non-portable cluster size)
 constexpr int kPb = 16;                    // panel width
 constexpr int kOwn = kTileMax / kCl;       // rows (and inverse columns) per CTA
 constexpr int kNpMax = kTileMax / kPb;     // panels per tile
 constexpr int kPotrfThreads = 256;
 constexpr int kLfN = kTileMax * (kTileMax + 1) / 2;
 constexpr int kDgLd = kPb + 1;
-static_assert(kOwn == kPb && kOwn * kPb == kPotrfThreads && kNpMax <= kCl, "thread layout");
-static_assert(kPotrfThreads == 256 && kOwn == 16, "the inverse's column pairs assume 8 warps x 2 columns");
+// (a) sends each CTA's kPb / kCl rows of a diagonal block with one thread per (row, column, CTA);
+// (c) takes a half-warp per own row, (d) kPotrfThreads / kOwn threads per row; the inverse takes
+// own-column pairs on warps 0 .. kOwn/2 - 1 (and their K ranges' second halves on the next
+// kOwn/2 warps); CTA b inverts diagonal block b.
+static_assert(kPotrfThreads == 256 && kPb * kPb == kPotrfThreads && kCl <= kPb && kPb <= 2 * kCl &&
+                  kOwn * kPb <= kPotrfThreads && kOwn % 2 == 0 && kOwn <= 16 && kNpMax <= kCl,
+              "thread layout");
+constexpr int kYt = kPb * (kOwn > kPb ? kOwn : kPb);  // Yt: kPb x kOwn, and the kPb x kPb block-inverse scratch
+// With few own columns (kOwn = 8), two warps share a column pair in the inverse, one per half of
+// its K range; Yt2 holds the second halves' sums.
+constexpr bool kSplitK = 2 * kOwn * kPb <= kPotrfThreads;
 constexpr size_t kPotrfSmem = sizeof(double) * (kLfN + kOwn * kTileMax + kPb * kDgLd + kTileMax +
-                                                kNpMax * kPb * kPb + kTileMax * kOwn + kPb * kOwn);
+                                                kNpMax * kPb * kPb + kTileMax * kOwn + kYt + (kSplitK ? kPb * kOwn : 0));
 
 // mbarrier helpers for the pipelined panel factorisation (shared memory, one CTA).
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -684,7 +693,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   double *rd = Dg + kPb * kDgLd;            // reciprocals of L's diagonal
   double *Li = rd + kTileMax;               // inverses of the diagonal blocks, [block][kPb][kPb]
   double *Xc = Li + kNpMax * kPb * kPb;     // own inverse columns c = rank + kCl * q: Xc[r * kOwn + q]
-  double *Yt = Xc + kTileMax * kOwn;        // kPb x kOwn temporary
+  double *Yt = Xc + kTileMax * kOwn;        // kPb x kOwn temporary (kYt doubles: also a kPb x kPb scratch)
+  double *Yt2 = Yt + kYt;                   // kPb x kOwn: the second halves of the K ranges (kSplitK)
   const int nown = rank < t ? (t - 1 - rank) / kCl + 1 : 0;
   const int np = (t + kPb - 1) / kPb;
   if (tid == 0) {
@@ -704,7 +714,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
     cluster.sync();  // every CTA resident (its shared memory exists) before any remote store
     for (int p = 0; p < np; ++p) {
       const int c0 = p * kPb, w = min(kPb, t - c0);
-      {  // (a) own rows of the diagonal block (c0 + rank and c0 + rank + kCl) to every CTA
+      {  // (a) own rows of the diagonal block (c0 + rank, and c0 + rank + kCl if kCl < kPb) to every CTA
         const int slot = tid / (kPb * kCl), c = (tid / kCl) % kPb, dst = tid % kCl;
         const int i = c0 + rank + kCl * slot;
         if (slot < 2 && i < c0 + w && c0 + c <= i) {
@@ -799,13 +809,15 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
         }
       }
       cluster.sync();  // every CTA's Lf holds the panel's columns of L
-      {  // (d) rank-kPb update of own trailing rows, 16 threads per row
-        const int li = tid / kPb, i = rank + kCl * li;
+      {  // (d) rank-kPb update of own trailing rows, kPotrfThreads / kOwn threads per row (a
+        // warp's FP64 issue rate bounds the longest row, so every warp takes part)
+        constexpr int kTpr = kPotrfThreads / kOwn;
+        const int li = tid / kTpr, i = rank + kCl * li;
         if (li < nown && i >= c0 + w) {
           double lrow[kPb];
 #pragma unroll
           for (int c = 0; c < kPb; ++c) lrow[c] = R[li * kTileMax + c0 + c];
-          for (int k = c0 + w + (tid % kPb); k <= i; k += kPb) {
+          for (int k = c0 + w + (tid % kTpr); k <= i; k += kTpr) {
             const double *lk = Lf + pk(k, c0);
             double v = R[li * kTileMax + k];
 #pragma unroll
@@ -851,18 +863,27 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   // column pairs are dealt so that the two warps of a sub-partition (w and
   // w + 4) hold one long and one short column pair between them.
   const int warp = tid >> 5, lane = tid & 31;
-  const int q0 = warp < 4 ? 2 * warp : 22 - 2 * warp;
+  // kSplitK: warps w and w + kOwn/2 take column pair w, the first and the second half of its K range
+  const int khalf = kSplitK ? warp / (kOwn / 2) : 0;
+  const int q0 = kSplitK ? 2 * (warp % (kOwn / 2)) : (warp < 4 ? 2 * warp : 22 - 2 * warp);
   const int rr = lane & 15, q = q0 + (lane >> 4), c = rank + kCl * q;
+  const bool qok = q < kOwn;
   for (int bi = 0; bi < np; ++bi) {
     const int r0 = bi * kPb, wb = min(kPb, t - r0), r = r0 + rr;
     double y = 0.0;
-    if (rr < wb && c < t && c <= r) {
-      y = (r == c) ? 1.0 : 0.0;
-      for (int k = c; k < r0; ++k) y = fma(-Lf[pk(r, k)], Xc[k * kOwn + q], y);
+    if (qok && rr < wb && c < t && c <= r) {
+      const int kmid = kSplitK ? (c + r0 + 1) / 2 : r0;  // [c, kmid) and [kmid, r0)
+      const int ka = khalf ? kmid : c, kb = khalf ? r0 : kmid;
+      y = (!khalf && r == c) ? 1.0 : 0.0;
+      for (int k = ka; k < kb; ++k) y = fma(-Lf[pk(r, k)], Xc[k * kOwn + q], y);
     }
-    Yt[rr * kOwn + q] = y;
+    if (qok) (khalf ? Yt2 : Yt)[rr * kOwn + q] = y;
     __syncthreads();
-    if (rr < wb) {
+    if (kSplitK) {
+      if (qok && !khalf) Yt[rr * kOwn + q] += Yt2[rr * kOwn + q];
+      __syncthreads();
+    }
+    if (qok && !khalf && rr < wb) {
       double x = 0.0;
       if (c <= r) {  // X(r, c) = 0 above the diagonal; never read there
         const double *Lb = Li + bi * kPb * kPb + rr * kPb;
@@ -1103,6 +1124,8 @@ cudaError_t tile_kernels_init() {
   if ((e = cudaFuncSetAttribute(k_tile<T_SENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem)))
     return e;
   if ((e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem)))
+    return e;
+  if (kCl > 8 && (e = cudaFuncSetAttribute(k_potrf_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)))
     return e;
   return cudaSuccess;
 }
