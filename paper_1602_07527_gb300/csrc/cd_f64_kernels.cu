@@ -533,11 +533,11 @@ constexpr int kPotrfThreads = 256;
 constexpr int kLfN = kTileMax * (kTileMax + 1) / 2;
 constexpr int kDgLd = kPb + 1;
 // (a) sends each CTA's kPb / kCl rows of a diagonal block with one thread per (row, column, CTA);
-// (c) takes a half-warp per own row, (d) kPotrfThreads / kOwn threads per row; the inverse takes
+// (c) takes a half-warp per own row on warps 4-7, (d) kPotrfThreads / kOwn threads per row; the inverse takes
 // own-column pairs on warps 0 .. kOwn/2 - 1 (and their K ranges' second halves on the next
 // kOwn/2 warps); CTA b inverts diagonal block b.
 static_assert(kPotrfThreads == 256 && kPb * kPb == kPotrfThreads && kCl <= kPb && kPb <= 2 * kCl &&
-                  kOwn * kPb <= kPotrfThreads && kOwn % 2 == 0 && kOwn <= 16 && kNpMax <= kCl,
+                  2 * kOwn * kPb <= kPotrfThreads && kOwn % 2 == 0 && kOwn <= 16 && kNpMax <= kCl,
               "thread layout");
 constexpr int kYt = kPb * (kOwn > kPb ? kOwn : kPb);  // Yt: kPb x kOwn, and the kPb x kPb block-inverse scratch
 // With few own columns (kOwn = 8), two warps share a column pair in the inverse, one per half of
@@ -774,7 +774,21 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
         }
       }
       __syncthreads();
-      if (tid < w) {  // pivots: sqrt(d) on L's diagonal, 1/sqrt(d) for the scaling and (c)
+      // The panel rows' substitution (c) needs 1/sqrt(d) only for its last multiply, so it runs on
+      // warps 4-7 while warp 0 takes the square roots.
+      const int li = (tid - kPotrfThreads / 2) / kPb, cs = tid % kPb, irow = rank + kCl * li;
+      const bool act = tid >= kPotrfThreads / 2 && li < nown && irow >= c0 + w;
+      double acc = act && cs < w ? R[li * kTileMax + c0 + cs] : 0.0;
+      if (tid >= kPotrfThreads / 2) {
+        // (c) own rows below the block: y = C U^{-T} with the unit-lower factor U = a / d by forward
+        // substitution across each half-warp (one FMA a step); L = y / sqrt(d) below.  A warp
+        // whose two rows are both above the panel or absent has nothing to solve.
+        if (__any_sync(0xffffffffu, act))
+          for (int s2 = 0; s2 + 1 < w; ++s2) {
+            const double ys = __shfl_sync(0xffffffffu, acc, s2, 16);
+            if (cs > s2 && cs < w) acc = fma(-ys, Ut[cs * kDgLd + s2], acc);
+          }
+      } else if (tid < w) {  // pivots: sqrt(d) on L's diagonal, 1/sqrt(d) for the scaling and (c)
         const double piv = Dg[tid * kDgLd + tid];
         const long long pb = __double_as_longlong(piv);
         const bool ok = pb > 0 && pb <= 0x7FF0000000000000ll;
@@ -788,25 +802,12 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
         const int r = e / w, c = e - r * w;
         if (r > c) Lf[pk(c0 + r, c0 + c)] = Dg[r * kDgLd + c] * rd[c0 + c];
       }
-      __syncthreads();
       if (s_bad >= 0) break;  // the same in every CTA: all factorised the same block
-      {  // (c) own rows below the block: y = C U^{-T} with the unit-lower factor U = a / d by
-        // forward substitution across each half-warp (one FMA a step), then L = y / sqrt(d)
-        const int li = tid / kPb, c = tid % kPb, i = rank + kCl * li;
-        const bool act = li < nown && i >= c0 + w;
-        double acc = act && c < w ? R[li * kTileMax + c0 + c] : 0.0;
-        // a warp whose two rows are both above the panel or absent has nothing to solve
-        if (__any_sync(0xffffffffu, act))
-          for (int s2 = 0; s2 + 1 < w; ++s2) {
-            const double ys = __shfl_sync(0xffffffffu, acc, s2, 16);
-            if (c > s2 && c < w) acc = fma(-ys, Ut[c * kDgLd + s2], acc);
-          }
-        const double lic = acc * rd[c0 + c];
-        if (act && c < w) {
-          R[li * kTileMax + c0 + c] = lic;
+      if (act && cs < w) {  // (c), finished: scale and send to every CTA's copy of L
+        const double lic = acc * rd[c0 + cs];
+        R[li * kTileMax + c0 + cs] = lic;
 #pragma unroll
-          for (int dst = 0; dst < kCl; ++dst) cluster.map_shared_rank(Lf, dst)[pk(i, c0 + c)] = lic;
-        }
+        for (int dst = 0; dst < kCl; ++dst) cluster.map_shared_rank(Lf, dst)[pk(irow, c0 + cs)] = lic;
       }
       cluster.sync();  // every CTA's Lf holds the panel's columns of L
       {  // (d) rank-kPb update of own trailing rows, kPotrfThreads / kOwn threads per row (a
