@@ -58,7 +58,7 @@ struct Arena {
 // split-BF16 ones are bound by their sequence of steps, and the FP64 ones
 // gain a little (chol_rev 1.176 -> 1.185, chol_fwd_sens 1.152 -> 1.159
 // TFLOP/s).  The factorisations (and the one-loop pass) prefer 128: their
-// diagonal blocks factorise on one cluster of at most 128 (FP64 chol_fwd 1.154 at
+// diagonal blocks (at most 128 wide) factorise on one cluster (FP64 chol_fwd 1.154 at
 // 128, 1.088 at 256).
 int pick_nb(int n, const cd_options *opt, bool factorisation = false) {
   int nb = (opt && opt->nb > 0) ? opt->nb : (n >= 1024 ? kDefaultNbLarge : kDefaultNbSmall);
