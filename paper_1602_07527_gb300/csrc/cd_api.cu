@@ -95,6 +95,7 @@ struct Prob {
   int col0;      // global column of this (sub)problem's first column (info)
   struct Mix {    // split-BF16 term arrays of the mixed path (null in FP64)
     void *big, *big2, *P1, *P2, *P3, *P4;
+    void *P5;  // reverse pass: two block columns of C_bar side by side (n x 2 nb), for the deferred r2
     long long ldb, ldn;
     int pad, T;
     // CD_MIXED_FIXED4 factorisation: fixed-point slices of L (fbig, rows of L),
@@ -1474,14 +1475,15 @@ size_t fixed_bytes(int n, int nb) {
   return 2 * (size_t)kFixedSlices * e + sizeof(int) * (2 * (size_t)n + nb) + 8 * kAlign;
 }
 
-size_t mix_bytes(int n, int nb, int T, bool two_big, bool fixed = false) {
+size_t mix_bytes(int n, int nb, int T, bool two_big, bool fixed = false, bool rev = false) {
   if (n <= 0) return 0;
   const size_t ldb = (size_t)((n + 8 + 63) / 64 * 64), ldn = (size_t)((n + 63) / 64 * 64 + 64);
-  const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + (size_t)nb * nb;
-  return 2 * (size_t)T * e + 8 * kAlign + (fixed ? fixed_bytes(n, nb) : 0);
+  const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + (size_t)nb * nb +
+                   (rev ? 2 * (size_t)n * nb : 0);
+  return 2 * (size_t)T * e + 9 * kAlign + (fixed ? fixed_bytes(n, nb) : 0);
 }
 
-bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bool fixed = false) {
+bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bool fixed = false, bool rev = false) {
   for (auto &p : P) {
     memset(&p.mx, 0, sizeof(p.mx));
     if (p.n <= 0) continue;
@@ -1497,7 +1499,9 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bo
     p.mx.P2 = ar.take(t * nb * p.mx.ldn);
     p.mx.P3 = ar.take(t * nb * p.mx.ldn);
     p.mx.P4 = ar.take(t * nb * nb);
-    if (!p.mx.big || (two_big && !p.mx.big2) || !p.mx.P1 || !p.mx.P2 || !p.mx.P3 || !p.mx.P4) return false;
+    p.mx.P5 = rev ? ar.take(t * n * 2 * nb) : nullptr;
+    if (!p.mx.big || (two_big && !p.mx.big2) || !p.mx.P1 || !p.mx.P2 || !p.mx.P3 || !p.mx.P4 || (rev && !p.mx.P5))
+      return false;
     if (fixed) {
       const size_t f = 2 * (size_t)kFixedSlices, ldf = (size_t)((n + 63) / 64 * 64);
       p.mx.fbig = ar.take(f * n * ldf);
@@ -1514,6 +1518,12 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bo
 
 // chol_blocked_rev (Sec. 4.2), products in split BF16.  L^T is split once
 // (columns shifted by pad so that every block boundary is a multiple of 8).
+//
+// r2 (B_bar <- B_bar - C_bar R) is deferred every other step ("the partitioning is arbitrary",
+// Sec. 4.2): an even step applies its C_bar R only to the block column of B_bar the next step
+// reads as its C_bar, and the next (odd) step applies both steps' parts to the rest in one
+// product with K = 2 nb, the two C_bar blocks side by side (columns [j, k + nb) of Sigma_bar,
+// split into P5).  B_bar's FP64 read-modify-write then happens once every two steps.
 void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
   precompute_dinv(c, P, nb, true, ar);
   {
@@ -1533,6 +1543,7 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
     return k > 0;
   };
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
+    const bool odd = s % 2 == 1;  // this step also applies the previous step's deferred r2
     {  // r1: C_bar <- C_bar D^{-1} (from the split copy of C_bar, so in place); then C_bar and C_bar^T split for r2, r3
       {
         SplitBatch sb(c);
@@ -1568,6 +1579,11 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
         // 64-wide K block are written (zeros past m), the rest is never read
         const int kw = (int)std::min<long long>(p.mx.ldn, (m + 63) / 64 * 64);
         sb.add(Cb, p.ldx, m, w, 0, 1, p.mx.P2, p.mx.ldn, nb, 0, 0, w, kw, 0, 0, T);
+        // odd step: the rows below the previous block, this C_bar and the previous one side by side
+        const int kp = std::min(p.n, k + nb);
+        if (odd && j > 0 && kp < p.n && p.mx.P5)
+          sb.add(p.X + (long long)kp * p.ldx + j, p.ldx, p.n - kp, kp - j, 0, 0, p.mx.P5, 2 * nb, p.n, 0, 0,
+                 p.n - kp, 2 * nb, 0, 0, T);
       }
     }
     c.fork();
@@ -1596,15 +1612,33 @@ void run_rev_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar) {
       }
     }
     c.mark();  // r5's second part waits for this point only
-    {  // r2 (side stream): B_bar <- B_bar - C_bar R
+    {  // r2 (side stream): B_bar <- B_bar - C_bar R, deferred every other step (see above)
       MixedBatch mb(c, T, false, true, "r2");
       for (auto &p : P) {
         int j, k;
-        if (!blk(p, s, j, k)) continue;
+        if (!blk(p, s, j, k) || j == 0) continue;
         const int w = k - j, m = p.n - k;
-        double *Bb = p.X + (long long)k * p.ldx;
-        mb.add(mop(p.mx.P1, nb, p.n, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), m, j, w, Bb, p.ldx,
-               Bb, p.ldx, -1.0, 1.0);
+        const MOp C = mop(p.mx.P1, nb, p.n, T, 0, 0);
+        if (!p.mx.P5) {  // no deferral
+          mb.add(C, mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), m, j, w, p.X + (long long)k * p.ldx, p.ldx,
+                 p.X + (long long)k * p.ldx, p.ldx, -1.0, 1.0);
+        } else if (!odd) {  // only columns [j - nb, j), which the next step reads; the rest waits
+          const int j0 = std::max(0, j - nb);
+          double *Bb = p.X + (long long)k * p.ldx + j0;
+          mb.add(C, mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, j0), m, j - j0, w, Bb, p.ldx, Bb, p.ldx, -1.0,
+                 1.0);
+        } else {
+          const int kp = std::min(p.n, k + nb);
+          double *Bb = p.X + (long long)k * p.ldx;
+          // rows [k, kp) (the previous block's rows): this step's part only
+          mb.add(C, mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), kp - k, j, w, Bb, p.ldx, Bb, p.ldx, -1.0, 1.0);
+          // rows [kp, n): this step's part and the previous step's deferred one, K = kp - j
+          if (kp < p.n) {
+            double *Bb2 = p.X + (long long)kp * p.ldx;
+            mb.add(mop(p.mx.P5, 2 * nb, p.n, T, 0, 0), mop(p.mx.big, p.mx.ldb, p.n, T, j + p.mx.pad, 0), p.n - kp, j,
+                   kp - j, Bb2, p.ldx, Bb2, p.ldx, -1.0, 1.0);
+          }
+        }
       }
     }
     {  // r4 as the products of Eq. symrevtril (problems that use them)
@@ -2160,7 +2194,7 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   if (opt.prec != CD_FP64)
     for (int b = 0; b < batch; ++b)
       need += mix_bytes(n[b], nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL,
-                        opt.prec == CD_MIXED_FIXED4 && factor);
+                        opt.prec == CD_MIXED_FIXED4 && factor, op == OP_REV);
   const bool upper = opt.uplo == CD_UPPER;
   const int narr = 1 + (factor ? 0 : 1) + (op == OP_DUAL ? 1 : 0);  // matrices per problem
   if (upper)
@@ -2230,7 +2264,8 @@ int run(cd_handle *h, Op op, int batch, const int *n, const double *const *L, co
   const bool fixed = opt.prec == CD_MIXED_FIXED4 && factor;
   if (mixed && mixed_init() != CD_OK) return CD_ECUDA;  // per device, once
   if (fixed && fixed_init() != CD_OK) return CD_ECUDA;
-  if (mixed && !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar, fixed)) return CD_ENOMEM;
+  if (mixed && !bind_mixed(P, nb, mix_terms(opt.prec), op == OP_SENS || op == OP_DUAL, ar, fixed, op == OP_REV))
+    return CD_ENOMEM;
   // The step loops issue the diagonal chain on the high-priority stream (its
   // CTAs are scheduled first when SM slots free up) and the independent bulk
   // GEMM of each step on the side stream; both start after, and the caller's
@@ -2414,7 +2449,7 @@ int cd_workspace_size(const cd_handle *h, int n_max, const cd_options *opt, size
   const int nb = pick_nb(n_max, opt);
   *bytes = need_bytes(&n_max, 1, nb, opt && opt->prec != CD_FP64, true) +
            ((opt && opt->prec != CD_FP64) ? mix_bytes(n_max, nb, mix_terms(opt->prec), true,
-                                                      opt->prec == CD_MIXED_FIXED4) : 0) +
+                                                      opt->prec == CD_MIXED_FIXED4, true) : 0) +
            ((opt && opt->uplo == CD_UPPER) ? 3 * (align_up(sizeof(double) * (size_t)n_max * n_max) + kAlign) : 0);
   return CD_OK;
 }
@@ -2430,7 +2465,7 @@ int cd_workspace_size_batched(const cd_handle *h, int batch, const int *n, const
   const bool mixed = opt && opt->prec != CD_FP64;
   size_t need = need_bytes(n, batch, nb, mixed, true);
   for (int b = 0; b < batch; ++b) {
-    if (mixed) need += mix_bytes(n[b], nb, mix_terms(opt->prec), true, opt->prec == CD_MIXED_FIXED4);
+    if (mixed) need += mix_bytes(n[b], nb, mix_terms(opt->prec), true, opt->prec == CD_MIXED_FIXED4, true);
     if (opt && opt->uplo == CD_UPPER) need += 3 * (align_up(sizeof(double) * (size_t)n[b] * n[b]) + kAlign);
   }
   *bytes = need;
