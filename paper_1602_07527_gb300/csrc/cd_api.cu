@@ -99,7 +99,9 @@ struct Prob {
     long long ldb, ldn;
     int pad, T;
     // CD_MIXED_FIXED4 factorisation: fixed-point slices of L (fbig, rows of L),
-    // of the panel (fP1) and of D^{-1} (fP4), with their row exponents
+    // of the panel (fP1) and of D^{-1} (fP4, two slots used by step parity: the
+    // diagonal tile writes step s's while the previous panel solve may still read
+    // step s-1's), with their row exponents
     void *fbig, *fP1, *fP4;
     int *exL, *exP1, *exP4;
   } mx;
@@ -560,6 +562,7 @@ TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double 
   TileDesc d;
   d.L = L; d.ldl = ldl; d.X = X; d.ldx = ldx; d.inv = inv; d.ldinv = ldinv;
   d.t = t; d.info = info; d.col0 = col0;
+  d.fsl = nullptr; d.fex = nullptr; d.ldf = 0; d.frows = 0; d.pad_ = 0;
   return d;
 }
 
@@ -1471,8 +1474,8 @@ int mix_terms(int prec) { return prec == CD_MIXED_BF16X3 ? 2 : 3; }
 size_t fixed_bytes(int n, int nb) {
   if (n <= 0) return 0;
   const size_t ldb = (size_t)((n + 63) / 64 * 64);
-  const size_t e = (size_t)n * ldb + (size_t)n * nb + (size_t)nb * nb;
-  return 2 * (size_t)kFixedSlices * e + sizeof(int) * (2 * (size_t)n + nb) + 8 * kAlign;
+  const size_t e = (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * nb;  // fP4: two slots
+  return 2 * (size_t)kFixedSlices * e + sizeof(int) * (2 * (size_t)n + 2 * nb) + 8 * kAlign;
 }
 
 size_t mix_bytes(int n, int nb, int T, bool two_big, bool fixed = false, bool rev = false) {
@@ -1506,10 +1509,10 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bo
       const size_t f = 2 * (size_t)kFixedSlices, ldf = (size_t)((n + 63) / 64 * 64);
       p.mx.fbig = ar.take(f * n * ldf);
       p.mx.fP1 = ar.take(f * n * nb);
-      p.mx.fP4 = ar.take(f * nb * nb);
+      p.mx.fP4 = ar.take(2 * f * nb * nb);  // two slots, by step parity
       p.mx.exL = (int *)ar.take(sizeof(int) * n);
       p.mx.exP1 = (int *)ar.take(sizeof(int) * n);
-      p.mx.exP4 = (int *)ar.take(sizeof(int) * nb);
+      p.mx.exP4 = (int *)ar.take(sizeof(int) * 2 * nb);
       if (!p.mx.fbig || !p.mx.fP1 || !p.mx.fP4 || !p.mx.exL || !p.mx.exP1 || !p.mx.exP4) return false;
     }
   }
@@ -1770,6 +1773,11 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
       }
     }
   };
+  // step t's D^{-1} slices and exponents (fixed4): slot t % 2
+  auto fP4s = [&](const Prob &p, int t) {
+    return (void *)((char *)p.mx.fP4 + (size_t)(t & 1) * 2 * kFixedSlices * nb * nb);
+  };
+  auto exP4s = [&](const Prob &p, int t) { return p.mx.exP4 + (size_t)(t & 1) * nb; };
   bool look_set[2] = {false, false};
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     const int j = s * nb;
@@ -1782,8 +1790,15 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
         const int w = std::min(p.n, j + nb) - j;
         double *D = p.X + (long long)j * p.ldx + j;
         if (w <= kTileMax) {
-          tb.add(tdesc(nullptr, 0, D, p.ldx, (j + w < p.n || dinv_slots) ? p.dinv + slot : nullptr, nb, w, p.info,
-                       p.col0 + j));
+          TileDesc td = tdesc(nullptr, 0, D, p.ldx, (j + w < p.n || dinv_slots) ? p.dinv + slot : nullptr, nb, w,
+                              p.info, p.col0 + j);
+          if (fx && j + w < p.n && nb <= kTileMax) {  // D^{-1} straight into the panel solve's slices
+            td.fsl = fP4s(p, s);
+            td.fex = exP4s(p, s);
+            td.ldf = nb;
+            td.frows = nb;
+          }
+          tb.add(td);
         } else {
           tb.flush();
           size_t mark = ar.off;
@@ -1807,8 +1822,8 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
         for (auto &p : P) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
-          if (p.n - j - w <= 0) continue;
-          sb.add(p.dinv + slot, nb, w, w, 0, p.mx.fP4, nb, nb, 0, 0, nb, nb, 0, 0, p.mx.exP4);
+          if (p.n - j - w <= 0 || (w <= kTileMax && nb <= kTileMax)) continue;  // the tile kernel wrote it
+          sb.add(p.dinv + slot, nb, w, w, 0, fP4s(p, s), nb, nb, 0, 0, nb, nb, 0, 0, exP4s(p, s));
         }
       } else {
         SplitBatch sb(c);
@@ -1832,7 +1847,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
         if (r1 <= r0) continue;
         double *Cb = p.X + (long long)(k + r0) * p.ldx + j;  // in place: the product reads only the split copies
         if (fx)
-          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, r0), fop(p.mx.fP4, nb, nb, p.mx.exP4, 0, 0), r1 - r0, w, w,
+          mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, r0), fop(fP4s(p, s), nb, nb, exP4s(p, s), 0, 0), r1 - r0, w, w,
                  nullptr, 0, Cb, p.ldx, 1.0, 0.0);
         else
           mb.add(mop(p.mx.P1, nb, p.n, T, 0, r0), mop(p.mx.P4, nb, nb, T, 0, 0), r1 - r0, w, w, nullptr, 0, Cb,

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "cd_internal.h"
+#include "cd_fixed_digits.cuh"
 
 namespace cd {
 
@@ -678,6 +679,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
   __shared__ __align__(8) uint64_t pub_bar, done_bar;
   __shared__ double acol[2 * kPb], ucol[2 * kPb];
   __shared__ double Ut[kPb * kDgLd];  // the panel's unit-lower factor a / d (below the diagonal)
+  __shared__ unsigned long long s_rmax[kTileMax];  // fixed-point output: row maxima of |X| (bits)
+  __shared__ int s_fex[kTileMax];                   // and the rows' exponents
   const TileDesc &d = g.d[blockIdx.y];
   const int t = d.t;
   // Both exits below are taken by every CTA of the cluster alike (same
@@ -893,6 +896,38 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
       Xc[r * kOwn + q] = x;
     }
     __syncthreads();
+  }
+  if (d.fsl != nullptr) {
+    // The inverse also in the fixed-point format of the tensor-core panel solve: row r's exponent
+    // from its largest |X(r, c)| over the cluster (each CTA's maximum over its own columns,
+    // gathered through distributed shared memory), then each CTA writes its own columns' slices
+    // (zero outside the tile's lower triangle, up to frows <= kTileMax rows and columns).
+    for (int r = tid; r < kTileMax; r += blockDim.x) {
+      unsigned long long m = 0;  // |x| as bits: ordered like the values
+      if (r < t)
+        for (int qq = 0; qq < kOwn; ++qq) {
+          const int cc = rank + kCl * qq;
+          if (cc <= r) m = max(m, (unsigned long long)__double_as_longlong(fabs(Xc[r * kOwn + qq])));
+        }
+      s_rmax[r] = m;
+    }
+    cluster.sync();
+    for (int r = tid; r < kTileMax; r += blockDim.x) {
+      unsigned long long m = 0;
+      for (int b = 0; b < kCl; ++b) m = max(m, cluster.map_shared_rank(s_rmax, b)[r]);
+      const int E = exp_above(__longlong_as_double((long long)m));
+      s_fex[r] = E;
+      if (rank == 0 && r < d.frows) d.fex[r] = E;
+    }
+    cluster.sync();  // every CTA has read every maximum; none is read after this
+    __nv_bfloat16 *fsl = (__nv_bfloat16 *)d.fsl;
+    const long long ts = (long long)d.frows * d.ldf;
+    for (int e = tid; e < d.frows * kOwn; e += blockDim.x) {
+      const int r = e / kOwn, qq = e - r * kOwn, cc = rank + kCl * qq;
+      if (cc >= d.frows) continue;
+      const double x = (r < t && cc <= r) ? Xc[r * kOwn + qq] : 0.0;
+      write_fixed_slices(fsl, ts, (long long)r * d.ldf + cc, fixed_q(x, s_fex[r]));
+    }
   }
   for (int e = tid; e < t * kOwn; e += blockDim.x) {
     const int r2 = e / kOwn, qq = e - r2 * kOwn, cc = rank + kCl * qq;

@@ -51,6 +51,7 @@
 #include "cd_internal.h"
 #include "cd_mixed.h"
 #include "cd_tc.cuh"
+#include "cd_fixed_digits.cuh"
 
 namespace cd {
 namespace {
@@ -503,15 +504,6 @@ __device__ __forceinline__ double view_value(const SplitArgs &a, int rr, int cc)
   return a.src[(long long)r * a.lds + c];
 }
 
-// Exponent E with 0 < x < 2^E for a non-negative binary64 x (the biased
-// exponent field gives x < 2^(field - 1022)); zero and subnormals give
-// kZeroExp, infinities and NaN 0.
-constexpr int kZeroExp = -1000;
-__device__ __forceinline__ int exp_above(double x) {
-  const int f = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
-  return f == 0 ? kZeroExp : f == 0x7FF ? 0 : f - 1022;
-}
-
 constexpr int kMaxFSplit = 24;
 struct SplitGroupF {
   int count, pad_;
@@ -548,23 +540,6 @@ __global__ void k_diagexp(const double *S, long long lds, int n, int *ex) {
   ex[i] = E;
 }
 
-// x 2^(31 - E) rounded to an integer (|x| < 2^E gives |Q| < 2^31), from the
-// bits of x; beyond the bound (not reached for valid exponents) it clamps.
-__device__ __forceinline__ long long fixed_q(double x, int E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0) return 0;
-  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-  const int sh = e - 1044 - E;  // x 2^(31 - E) = m 2^(e - 1075 + 31 - E)
-  long long q;
-  if (e == 0x7FF || sh >= 0)
-    q = 0x7FFFFFFFll;
-  else
-    q = sh < -63 ? 0 : ((m >> (-sh - 1)) + 1) >> 1;
-  q = min(q, 0x7FFFFFFFll);
-  return (b >> 63) ? -q : q;
-}
-
 // Fixed-point split: 32 x 32 destination tiles, slice s of element (r, c) at
 // dst + (s dst_rows + r) ldd + c, each a_s 2^(-8 s) with a_s in [-128, 128]:
 // Q = a_0 2^24 + a_1 2^16 + a_2 2^8 + a_3, digits taken from the top.
@@ -580,18 +555,7 @@ __global__ void __launch_bounds__(256) k_fsplit_group(const __grid_constant__ Sp
       const int rr = rr0 + (e >> 5), cc = cc0 + (e & 31);
       if (rr >= a.dst_h || cc >= a.dst_w) continue;
       const int row = a.reg_r0 + rr;
-      long long q = fixed_q(view_value(a, rr, cc), a.ex[row]);
-      const long long a0 = (q + (1ll << 23)) >> 24;
-      q -= a0 << 24;
-      const long long a1 = (q + (1ll << 15)) >> 16;
-      q -= a1 << 16;
-      const long long a2 = (q + (1ll << 7)) >> 8;
-      q -= a2 << 8;
-      const long long o = (long long)row * a.ldd + a.reg_c0 + cc;
-      dst[o] = __float2bfloat16_rn((float)a0);
-      dst[ts + o] = __float2bfloat16_rn((float)a1 * 0x1p-8f);
-      dst[2 * ts + o] = __float2bfloat16_rn((float)a2 * 0x1p-16f);
-      dst[3 * ts + o] = __float2bfloat16_rn((float)q * 0x1p-24f);
+      write_fixed_slices(dst, ts, (long long)row * a.ldd + a.reg_c0 + cc, fixed_q(view_value(a, rr, cc), a.ex[row]));
     }
   }
 }

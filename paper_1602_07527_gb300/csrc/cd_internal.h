@@ -81,6 +81,12 @@ struct TileDesc {
   int *info;        // potf2: info word of the problem (may be null)
   long long ldl, ldx, ldinv;
   int t, col0;      // tile size; global column of the tile's first column
+  // optional (T_POTRF with inv): the inverse also as fixed-point slices (cd_fixed_digits.cuh), slice s
+  // of (r, c) at fsl + (s frows + r) ldf + c for r, c < frows, and the row exponents fex[0, frows)
+  void *fsl;
+  int *fex;
+  long long ldf;
+  int frows, pad_;
 };
 
 constexpr int kMaxTile = 48;
@@ -89,7 +95,7 @@ struct TileGroup {
   int *err;  // device error word: CD_ETIMEOUT if a bounded wait of the cluster kernel runs out
   TileDesc d[kMaxTile];
 };
-static_assert(sizeof(TileGroup) <= 4096, "kernel parameter block too large");
+static_assert(sizeof(TileGroup) <= 32764, "kernel parameter block too large");
 
 // T_REV / T_SENS: the level-2 derivative loops on one CTA.  T_POTRF: the
 // diagonal tile on a cluster of CTAs: factorise X in place (info set at the
