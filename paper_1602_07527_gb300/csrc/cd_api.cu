@@ -562,7 +562,7 @@ TileDesc tdesc(const double *L, long long ldl, double *X, long long ldx, double 
   TileDesc d;
   d.L = L; d.ldl = ldl; d.X = X; d.ldx = ldx; d.inv = inv; d.ldinv = ldinv;
   d.t = t; d.info = info; d.col0 = col0;
-  d.fsl = nullptr; d.fex = nullptr; d.ldf = 0; d.frows = 0; d.pad_ = 0;
+  d.fsl = nullptr; d.fex = nullptr; d.ldf = 0; d.frows = 0; d.fterms = 0;
   return d;
 }
 
@@ -1481,7 +1481,7 @@ size_t fixed_bytes(int n, int nb) {
 size_t mix_bytes(int n, int nb, int T, bool two_big, bool fixed = false, bool rev = false) {
   if (n <= 0) return 0;
   const size_t ldb = (size_t)((n + 8 + 63) / 64 * 64), ldn = (size_t)((n + 63) / 64 * 64 + 64);
-  const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + (size_t)nb * nb +
+  const size_t e = (two_big ? 2 : 1) * (size_t)n * ldb + (size_t)n * nb + 2 * (size_t)nb * ldn + 2 * (size_t)nb * nb +
                    (rev ? 2 * (size_t)n * nb : 0);
   return 2 * (size_t)T * e + 9 * kAlign + (fixed ? fixed_bytes(n, nb) : 0);
 }
@@ -1501,7 +1501,7 @@ bool bind_mixed(std::vector<Prob> &P, int nb, int T, bool two_big, Arena &ar, bo
     p.mx.P1 = ar.take(t * n * nb);
     p.mx.P2 = ar.take(t * nb * p.mx.ldn);
     p.mx.P3 = ar.take(t * nb * p.mx.ldn);
-    p.mx.P4 = ar.take(t * nb * nb);
+    p.mx.P4 = ar.take(2 * t * nb * nb);  // two slots: the factorisation's D^{-1} by step parity
     p.mx.P5 = rev ? ar.take(t * n * 2 * nb) : nullptr;
     if (!p.mx.big || (two_big && !p.mx.big2) || !p.mx.P1 || !p.mx.P2 || !p.mx.P3 || !p.mx.P4 || (rev && !p.mx.P5))
       return false;
@@ -1778,6 +1778,8 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
     return (void *)((char *)p.mx.fP4 + (size_t)(t & 1) * 2 * kFixedSlices * nb * nb);
   };
   auto exP4s = [&](const Prob &p, int t) { return p.mx.exP4 + (size_t)(t & 1) * nb; };
+  // the same for the three-term split: the previous panel solve may still read step t-1's
+  auto P4s = [&](const Prob &p, int t) { return (void *)((char *)p.mx.P4 + (size_t)(t & 1) * 2 * T * nb * nb); };
   bool look_set[2] = {false, false};
   for (int s = 0; s < steps && c.err == CD_OK; ++s) {
     const int j = s * nb;
@@ -1792,9 +1794,10 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
         if (w <= kTileMax) {
           TileDesc td = tdesc(nullptr, 0, D, p.ldx, (j + w < p.n || dinv_slots) ? p.dinv + slot : nullptr, nb, w,
                               p.info, p.col0 + j);
-          if (fx && j + w < p.n && nb <= kTileMax) {  // D^{-1} straight into the panel solve's slices
-            td.fsl = fP4s(p, s);
-            td.fex = exP4s(p, s);
+          if (j + w < p.n && nb <= kTileMax) {  // D^{-1} straight into the panel solve's operand
+            td.fsl = fx ? fP4s(p, s) : P4s(p, s);
+            td.fex = fx ? exP4s(p, s) : nullptr;
+            td.fterms = fx ? 0 : T;
             td.ldf = nb;
             td.frows = nb;
           }
@@ -1830,8 +1833,8 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
         for (auto &p : P) {
           if (j >= p.n) continue;
           const int w = std::min(p.n, j + nb) - j;
-          if (p.n - j - w <= 0) continue;
-          sb.add(p.dinv + slot, nb, w, w, 0, 0, p.mx.P4, nb, nb, 0, 0, nb, nb, 0, 0, T);
+          if (p.n - j - w <= 0 || (w <= kTileMax && nb <= kTileMax)) continue;  // the tile kernel wrote it
+          sb.add(p.dinv + slot, nb, w, w, 0, 0, P4s(p, s), nb, nb, 0, 0, nb, nb, 0, 0, T);
         }
       }
     }
@@ -1850,7 +1853,7 @@ void run_fwd_mixed(Ctx &c, std::vector<Prob> &P, int nb, Arena &ar,
           mb.add(fop(p.mx.fP1, nb, p.n, p.mx.exP1, 0, r0), fop(fP4s(p, s), nb, nb, exP4s(p, s), 0, 0), r1 - r0, w, w,
                  nullptr, 0, Cb, p.ldx, 1.0, 0.0);
         else
-          mb.add(mop(p.mx.P1, nb, p.n, T, 0, r0), mop(p.mx.P4, nb, nb, T, 0, 0), r1 - r0, w, w, nullptr, 0, Cb,
+          mb.add(mop(p.mx.P1, nb, p.n, T, 0, r0), mop(P4s(p, s), nb, nb, T, 0, 0), r1 - r0, w, w, nullptr, 0, Cb,
                  p.ldx, 1.0, 0.0);
       }
     };

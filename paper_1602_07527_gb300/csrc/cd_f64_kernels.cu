@@ -16,6 +16,7 @@
 
 #include "cd_internal.h"
 #include "cd_fixed_digits.cuh"
+#include "cd_split_terms.cuh"
 
 namespace cd {
 
@@ -897,7 +898,17 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kPotrfThreads, 1)
     }
     __syncthreads();
   }
-  if (d.fsl != nullptr) {
+  if (d.fsl != nullptr && d.fterms > 0) {  // the inverse also as the split-BF16 terms of the panel solve
+    __nv_bfloat16 *tsl = (__nv_bfloat16 *)d.fsl;
+    const long long ts = (long long)d.frows * d.ldf;
+    for (int e = tid; e < d.frows * kOwn; e += blockDim.x) {
+      const int r = e / kOwn, qq = e - r * kOwn, cc = rank + kCl * qq;
+      if (cc >= d.frows) continue;
+      float hi, lo;
+      f64_to_f32x2((r < t && cc <= r) ? Xc[r * kOwn + qq] : 0.0, hi, lo);
+      write_split_terms(tsl, ts, (long long)r * d.ldf + cc, hi, lo, d.fterms);
+    }
+  } else if (d.fsl != nullptr) {
     // The inverse also in the fixed-point format of the tensor-core panel solve: row r's exponent
     // from its largest |X(r, c)| over the cluster (each CTA's maximum over its own columns,
     // gathered through distributed shared memory), then each CTA writes its own columns' slices

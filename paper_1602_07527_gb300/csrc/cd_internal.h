@@ -81,12 +81,14 @@ struct TileDesc {
   int *info;        // potf2: info word of the problem (may be null)
   long long ldl, ldx, ldinv;
   int t, col0;      // tile size; global column of the tile's first column
-  // optional (T_POTRF with inv): the inverse also as fixed-point slices (cd_fixed_digits.cuh), slice s
-  // of (r, c) at fsl + (s frows + r) ldf + c for r, c < frows, and the row exponents fex[0, frows)
+  // optional (T_POTRF with inv): the inverse also in a tensor-core operand format, slice or term s
+  // of (r, c) at fsl + (s frows + r) ldf + c for r, c < frows: fterms = 0, fixed-point slices
+  // (cd_fixed_digits.cuh) with the row exponents fex[0, frows); fterms = 2 or 3, that many BF16
+  // terms of the split-BF16 products (cd_split_terms.cuh)
   void *fsl;
   int *fex;
   long long ldf;
-  int frows, pad_;
+  int frows, fterms;
 };
 
 constexpr int kMaxTile = 48;

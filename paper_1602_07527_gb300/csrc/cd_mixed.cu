@@ -28,6 +28,7 @@
 #include "cd_internal.h"
 #include "cd_mixed.h"
 #include "cd_tc.cuh"
+#include "cd_split_terms.cuh"
 
 namespace cd {
 namespace {
@@ -67,31 +68,6 @@ static_assert(sizeof(MGroup) <= 4096, "kernel parameter block too large");
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
 
-// binary64 x -> (hi, lo) in binary32: hi is x with its significand cut to 24
-// bits (exact), lo the remaining 29 bits rounded to 24, so that
-// |x - hi - lo| <= 2^-47 |x|.  Outside FP32's normal range: below it both
-// parts are zero, above it hi is +-inf, NaN stays NaN.
-__device__ __forceinline__ void f64_to_f32x2(double x, float &hi, float &lo) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const uint32_t sg = (uint32_t)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7FF);
-  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
-  const int fe = e - 896;  // binary32 biased exponent of x
-  lo = 0.0f;
-  if (fe >= 1 && fe <= 254) {
-    hi = __uint_as_float(sg | ((uint32_t)fe << 23) | (uint32_t)(m >> 29));
-    const uint32_t r = (uint32_t)(m & 0x1FFFFFFFu);  // remainder r 2^(e - 1075)
-    if (r != 0) {
-      const uint32_t rb = __float_as_uint(__uint2float_rn(r));
-      const int re = (int)(rb >> 23) + (e - 1075);  // rescale through the exponent field
-      if (re >= 1) lo = __uint_as_float(sg | ((uint32_t)re << 23) | (rb & 0x7FFFFFu));
-    }
-  } else if (e == 0x7FF) {
-    hi = __uint_as_float(sg | 0x7F800000u | (m ? 0x400000u : 0u));
-  } else {
-    hi = __uint_as_float(fe > 254 ? (sg | 0x7F800000u) : sg);
-  }
-}
 
 // The epilogue stages each warp's accumulators 32 rows x kEpiCols columns at
 // a time (lane = row on the way in), so that the output can be written with
@@ -548,15 +524,8 @@ __device__ __forceinline__ void split_load(const SplitArgs &a, int rr, int cc, f
 
 // The T BF16 terms of one element from its FP32 pieces.
 __device__ __forceinline__ void split_store(const SplitArgs &a, int rr, int cc, float hi, float lo) {
-  __nv_bfloat16 *dst = (__nv_bfloat16 *)a.dst;
-  const long long tstride = a.dst_rows * a.ldd;
-  const long long o = (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc;
-  const __nv_bfloat16 t0 = __float2bfloat16_rn(hi);
-  const float d0 = hi - __bfloat162float(t0);
-  const __nv_bfloat16 t1 = __float2bfloat16_rn(d0 + lo);
-  dst[o] = t0;
-  dst[tstride + o] = t1;
-  if (a.T == 3) dst[2 * tstride + o] = __float2bfloat16_rn((d0 - __bfloat162float(t1)) + lo);
+  write_split_terms((__nv_bfloat16 *)a.dst, a.dst_rows * a.ldd, (long long)(a.reg_r0 + rr) * a.ldd + a.reg_c0 + cc,
+                    hi, lo, a.T);
 }
 
 // cuTensorMapEncodeTiled is a driver entry point; it is looked up through the
