@@ -200,7 +200,11 @@ int cd_chol_fwd_sens(cd_handle *h, int n, const double *L, long long ldl,
  * L, Eq. symfwd.  A and Adot must not overlap.  info as for cd_chol_fwd; on a
  * non-positive pivot both outputs are unspecified from that column on.
  * Blocking, precision (split-BF16 products for CD_MIXED_*) and the diagonal
- * routine follow options as for the two separate calls.
+ * routine follow options as for the two separate calls.  Both halves use the
+ * factorisation's block size; each forward-mode block step is issued as soon
+ * as the factorisation has finished its block column and runs beside it on a
+ * second pair of the handle's internal streams, so the call takes less time
+ * than the two separate calls.
  */
 int cd_chol_fwd_and_sens(cd_handle *h, int n, double *A, long long lda, double *Adot, long long ldadot,
                          const cd_options *opt, void *stream, int *info);
