@@ -526,6 +526,12 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const __grid_constant__ T
 // inverts diagonal block b (a forward-substitution sweep per column, again
 // across half-warps) and sends it to all; each CTA then forms its own columns
 // of X = L^{-1} block row by block row, X_bi = D_bi^{-1} (E - L_{bi,<bi} X_{<bi}).
+// On request (TileDesc::fsl) X is also written in the operand format of the
+// tensor-core panel solve that consumes it: the split-BF16 terms of each
+// element, or fixed-point slices, whose per-row exponents take the row's
+// largest |X| over the cluster (each CTA's maximum over its own columns,
+// gathered through distributed shared memory).  That saves the mixed
+// factorisation a split launch on its diagonal chain at every block step.
 // ---------------------------------------------------------------------------
 constexpr int kCl = 16;                    // CTAs per tile (a non-portable cluster size)
 constexpr int kPb = 16;                    // panel width
